@@ -1,0 +1,374 @@
+#!/usr/bin/env python3
+"""Benchmark of one Blahut-Arimoto iteration on BDC_d at n = 24.
+
+Metric: W(y|x) pair-evaluations per second (effective: the 2*3^n - 2^n
+(input, distinct output) pairs an iteration covers, divided by the time of
+one iteration) and milliseconds per BA iteration.  A step is one full BA
+iteration (output marginal, log, divergence, bounds, update) of the n=24,
+d=0.5 instance in FP32 on the factorised sweep, with every input resident in
+HBM; the FP64 sweep, the FP64 literal enumeration (the plain FP64 GPU form),
+the FP64 certificate and the d-free precompute are timed beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun, one rank per GPU): every rank runs its own instance
+(instances are independent: weak scaling, no data-path collective); the
+reported time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "W(y|x) pair-evals/s and s/BA-iteration at n=24, FP32+FP64-certify vs FP64"
+UNIT = "pair-evals/s"
+N_BITS = int(os.environ.get("BDC_BENCH_N", "24"))
+D_VALUE = 0.5
+
+
+def pairs_per_iteration(n: int) -> int:
+    """(input, distinct output) pairs one BA iteration covers: sum_x N_x = 2*3^n - 2^n."""
+    return 2 * 3 ** n - 2 ** n
+
+
+def stage_bytes(n: int, n1: int, n2: int, elem: int) -> dict:
+    """Algorithmic HBM bytes of each sweep stage (unique values each launch must
+    read or write once, all instances of the step), in units of bytes."""
+    N = 1 << n
+    split = n2 > 0
+    return {
+        # p and Dbar in, updated p and F1 (rows below 2^n1) out
+        "cols_fwd": (4 if split else 3) * N * elem + (0 if split else 4 * N * elem),
+        # every row (F1 or p) in, bottom half of every row out
+        "rows_fwd": 4 * N * elem,
+        # every (u1, u2) pair in once, q and log2 q out
+        "combine": 8 * N * elem,
+        # log2 q in (its re-reads are L2 hits), Gb out
+        "rows_adj": 4 * N * elem,
+        # Gb, Hb, p in, D out (single pass: L, Hb, p in, D out)
+        "cols_adj": 5 * N * elem,
+        "symmetrize": 2 * N * elem,
+        "finalize": 0,
+    }
+
+
+# ----------------------------------------------------------------------------
+# clocks
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--id=" + self.gpu_id, "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [s.strip() for s in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            j = json.load(f)
+        return {"hbm_gbs": float(j["hbm_gbs"]), "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6400.0, "source": "fallback"}
+
+
+# ----------------------------------------------------------------------------
+# oracle timing (host cores) -- the CPU baseline and the reference arm
+# ----------------------------------------------------------------------------
+def oracle_rate(n: int, d: float, seconds: float, seed: int = 0):
+    """Time the FP64 oracle's divergence walk on random inputs of length n
+    until about `seconds` of work; returns (pair-evals/s for a full iteration,
+    cores, sample description).  A BA iteration of the oracle walks every
+    (x, distinct y) pair twice (output marginal, then divergence) at the same
+    cost per pair, so the full-iteration rate is half the walk rate."""
+    import oracle
+    from paper_2604_05867_b300 import inputs
+
+    q = np.ones(2 << n)  # any positive q: the walk's cost does not depend on its values
+    q[0] = 0.0
+    size, total_pairs, total_t, total_x = 32, 0, 0.0, 0
+    it = 0
+    while total_t < seconds:
+        xs = inputs.random_inputs(n, size, seed=seed + it).astype(np.uint64)
+        t0 = time.perf_counter()
+        _, pr = oracle.D_list(n, d, q, xs)
+        dt = time.perf_counter() - t0
+        total_pairs += pr
+        total_t += dt
+        total_x += size
+        it += 1
+        if dt < seconds / 8:
+            size *= 2
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    rate = total_pairs / total_t / 2.0
+    sample = ("divergence walk of the FP64 oracle (OpenMP) over %d random inputs of length %d, %d pairs in %.1f s; "
+              "full-iteration rate = half the walk rate (marginal + divergence passes)" % (total_x, n, total_pairs,
+                                                                                           total_t))
+    return rate, cores, sample, total_t
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    n = N_BITS
+    per_step = []
+    rates = []
+    cores = None
+    for s in range(args.warmup + args.steps):
+        budget = 0.5 if s < args.warmup else max(0.5, min(3.0, 150.0 / max(1, args.steps)))
+        r, cores, sample, t = oracle_rate(n, D_VALUE, budget, seed=1000 * s)
+        if s >= args.warmup:
+            rates.append(r)
+            per_step.append(pairs_per_iteration(n) / r)
+    value = float(statistics.median(rates))
+    ms = 1000.0 * pairs_per_iteration(n) / value
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "BA iteration on BDC_d, n=24, d=0.5 (all 2^24 inputs)", "n": n, "d": [D_VALUE],
+                   "parallelism": "host cores (OpenMP)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "per step: " + sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+def run_ours(args, rank: int, world: int):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2604_05867_b300 as bdc
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    n, d = N_BITS, D_VALUE
+
+    with torch.cuda.stream(stream):
+        t0 = time.perf_counter()
+        eng = bdc.Engine(n, [d], options=bdc.default_options(enable_literal=1, chunk=8), stream=stream)
+        a0_s = time.perf_counter() - t0
+
+        # warm-up: W untimed FP32 iterations
+        eng.iterate(args.warmup, -1.0, "fp32", "sweep")
+        torch.cuda.synchronize()
+
+        props = torch.cuda.get_device_properties(dev)
+        gpu_id = getattr(props, "pci_bus_id", None)
+        gpu_id = str(gpu_id) if gpu_id else str(local)
+        clocks = ClockSampler(gpu_id)
+        clocks.start()
+        time.sleep(0.5)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        launches0 = eng.launch_count()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        lo, up, it = eng.iterate(args.steps, -1.0, "fp32", "sweep")
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ms_total = ev0.elapsed_time(ev1)
+        launches = eng.launch_count() - launches0
+        clk = clocks.stop()
+        ms = ms_total / args.steps
+        if world > 1:
+            t = torch.tensor([ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        value = pairs_per_iteration(n) * world / (ms / 1000.0)
+
+        extra = {}
+        if rank == 0:
+            # per-stage times (events after every kernel, no graph), same workload
+            stages = eng.profile("fp32", "sweep", reps=5)
+            sched = (None, None)
+            n2 = 14 if n >= 15 else 0
+            n1 = n - n2
+            sb = stage_bytes(n, n1, n2, 4)
+            peaks = measured_peaks()
+            top = max((k for k in stages if k in sb and sb[k] > 0), key=lambda k: stages[k])
+            achieved = sb[top] / (stages[top] / 1000.0) / 1e9
+            roof = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                    "peak_source": peaks["source"], "algorithmic_bytes": sb[top]}
+            stage_total = sum(stages.values())
+
+            # FP64 sweep iteration (same-algorithm precision baseline)
+            eng.iterate(2, -1.0, "fp64", "sweep")
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            eng.iterate(5, -1.0, "fp64", "sweep")
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms64 = e0.elapsed_time(e1) / 5
+
+            # FP64 certificate of the current p
+            e0.record(stream)
+            cert = eng.certify()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_cert = e0.elapsed_time(e1)
+
+            # plain FP64 GPU form: literal enumeration (orbit representatives)
+            ms_lit = None
+            if not args.skip_literal:
+                e0.record(stream)
+                eng.iterate(1, -1.0, "fp64", "literal")
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms_lit = e0.elapsed_time(e1)
+            eng.iterate(1, -1.0, "fp32", "sweep")  # back to the FP32 representation
+
+            # end to end through the public API: one Engine.iterate(1) call per
+            # step, bounds read back to the host every step
+            K = max(10, min(args.steps, 50))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(K):
+                eng.iterate(1, -1.0, "fp32", "sweep")
+            e2e_s = (time.perf_counter() - t0) / K
+            extra = {
+                "roofline": roof,
+                "stages_ms": stages,
+                "stage_sum_ms": stage_total,
+                "forms": {
+                    "fp32_sweep_ms_per_iter": ms,
+                    "fp64_sweep_ms_per_iter": ms64,
+                    "fp64_literal_ms_per_iter": ms_lit,
+                    "fp64_certify_ms": ms_cert,
+                    "precompute_a0_s": a0_s,
+                    "speedup_fp32_vs_fp64_sweep": ms64 / ms,
+                    "speedup_fp32_sweep_vs_fp64_literal": (ms_lit / ms) if ms_lit else None,
+                    "speedup_fp64_sweep_vs_fp64_literal": (ms_lit / ms64) if ms_lit else None,
+                    "certified_upper_over_n": float(cert["upper"][0]) / n,
+                    "certify_margin_bits": float(cert["margin"][0]),
+                    "lower_after_run": float(lo[0]), "upper_after_run": float(up[0]),
+                },
+                "e2e": {"value": pairs_per_iteration(n) / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 32 * 8, "ms_per_step": e2e_s * 1000.0,
+                        "call": "Engine.iterate(1) -> bdc_ba_iterate, bounds read back each step"},
+            }
+            if world == 1 and not args.skip_cpu:
+                rate, cores, sample, _ = oracle_rate(n, d, args.cpu_seconds)
+                extra["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                         "sample": sample}
+        eng.close()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "BA iteration on BDC_d, n=24, d=0.5 (all 2^24 inputs), FP32 factorised sweep",
+                       "n": n, "d": [d], "instances_per_gpu": 1, "parallelism": "instance-parallel",
+                       "l2": "inputs larger than L2 (per-iteration working set ~0.8 GB vs 126 MB L2)",
+                       "step": "one BA iteration: q sweep, log2, adjoint sweep, D, bounds, orbit mean, p update"},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+        }
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-literal", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        if args.impl == "reference":
+            if rank != 0:
+                return
+        else:
+            import torch
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+            dist.init_process_group("nccl")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+    if world > 1 and args.impl != "reference":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

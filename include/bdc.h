@@ -1,0 +1,209 @@
+/*
+ * bdc.h -- C ABI of the B300 Blahut-Arimoto engine for the finite-length
+ * binary deletion channel BDC_d (inputs {0,1}^n, outputs {0,1}^{<=n}).
+ *
+ * The operation (paper Sec. 2.3, in the log2 form of Sec. 3): for an input
+ * distribution p over {0,1}^n,
+ *     q(y)  = sum_x p(x) W(y|x),   W(y|x) = Count(y,x) d^(n-|y|) (1-d)^|y|
+ *     D_x   = sum_y W(y|x) log2(W(y|x)/q(y))
+ *     lower = log2 sum_x p(x) 2^{D_x}      upper = max_x D_x
+ *     p    <- p 2^{D} / sum_x p 2^{D}
+ * where Count(y,x) is the number of times y appears as a subsequence of x
+ * (Sec. 2.2).  C_n(d)/n is an upper bound on the deletion-channel capacity
+ * C(d) (Sec. 2.2, first lemma); upper is a valid upper bound on C_n(d) for
+ * every p (the dual/minimax bound; certified in FP64 by bdc_certify_upper).
+ *
+ * Encoding: x in {0,1}^n is the integer whose most significant of n bits is
+ * x_0 (lexicographic order = numeric order).  An output y of length k has the
+ * code (1<<k)|y; codes lie in [1, 2^(n+1)), code 1 is the empty output and
+ * slot 0 of every code-indexed array is unused (0).  Logs are base 2 (Sec. 2.1).
+ *
+ * Memory: the library never allocates device memory on the engine path.  The
+ * caller allocates one device workspace of bdc_workspace_bytes() and binds it
+ * with a CUDA stream; every kernel runs on that stream, in stream order.
+ * Host pointers are read or written before the call returns.  Calls on one
+ * engine must not overlap.  Errors are returned as bdc_status codes; no C++
+ * exception crosses the ABI; bdc_last_error() gives a thread-local message.
+ */
+#ifndef BDC_H
+#define BDC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BDC_OK = 0,
+    BDC_EINVAL = -1,      /* bad argument (sizes, ranges, NULL) */
+    BDC_ENOMEM = -2,      /* workspace too small */
+    BDC_ECUDA = -3,       /* a CUDA runtime call or kernel launch failed */
+    BDC_ETIMEOUT = -4,    /* a bounded device wait gave up */
+    BDC_ENONFINITE = -5,  /* a NaN/Inf reached a reduction */
+    BDC_ENOTBOUND = -6    /* no workspace bound yet */
+} bdc_status;
+
+enum { BDC_FP32 = 0, BDC_FP64 = 1 };       /* precision of the iteration */
+enum { BDC_SWEEP = 0, BDC_LITERAL = 1 };   /* algorithm of the iteration */
+
+typedef struct bdc_engine bdc_engine;
+
+typedef struct {
+    /* Replace D by its mean over the complement/reversal orbit of x before
+     * every p update (Appendix A: the iterates are orbit-invariant in exact
+     * arithmetic; this removes rounding drift).  Default 1. */
+    int symmetrize;
+    /* Capture one iteration of all instances in a CUDA graph and replay it.
+     * Default 1. */
+    int use_graph;
+    /* Iterations per graph launch when use_graph (default 8).  The host reads
+     * the per-instance stop flags after each launch. */
+    int chunk;
+    /* Floor applied to the per-length output marginal before its log (FP32
+     * iterations only; keeps log2 finite if p underflowed).  Default 1e-30. */
+    double q_floor;
+    /* Weight of the uniform input mixed into p before certification, so the
+     * certified output distribution is positive everywhere.  Default 2^-30. */
+    double certify_mix;
+    /* Row-sweep length n2 and column tile width override for the sweep
+     * schedule (0 = automatic). */
+    int sched_n2_fp32, sched_w_fp32, sched_n2_fp64, sched_w_fp64;
+    /* Reserve the buffers of the literal (enumeration) path.  Default 1. */
+    int enable_literal;
+} bdc_options;
+
+/* Fill *opt with the defaults above. */
+void bdc_default_options(bdc_options *opt);
+
+/* --- lifecycle ---------------------------------------------------------- */
+
+/* Create an engine for input length n (1 <= n <= 26) and nd >= 1 deletion
+ * probabilities d[0..nd) in [0,1] (copied).  opt may be NULL (defaults).
+ * Runs no kernel.  *out is owned by the caller (bdc_destroy). */
+bdc_status bdc_create(int n, const double *d, int nd, const bdc_options *opt, bdc_engine **out);
+
+/* Bytes of device workspace the engine needs (0 on NULL). */
+size_t bdc_workspace_bytes(const bdc_engine *eng);
+
+/* Bind a caller-owned device workspace (>= bdc_workspace_bytes, 256-byte
+ * aligned) and a cudaStream_t (NULL = legacy default stream).  The engine
+ * does not own the memory and must not outlive it.  Runs the d-free
+ * precompute (orbit representatives; per representative x and length k the
+ * number of distinct subsequences N_{x,k} and S_k(x) = sum count*log2(count),
+ * Sec. 4.1 and Appendix A), the per-d entropy term, and sets p to uniform
+ * (Sec. 2.3).  Synchronous. */
+bdc_status bdc_bind(bdc_engine *eng, void *dev_workspace, size_t bytes, void *cuda_stream);
+
+/* Free the host-side engine object (not the workspace). */
+void bdc_destroy(bdc_engine *eng);
+
+/* --- iteration ---------------------------------------------------------- */
+
+/* Run up to max_iters BA iterations (Sec. 2.3) on every instance, in the
+ * given precision (BDC_FP32 / BDC_FP64) and algorithm (BDC_SWEEP: factorised
+ * forward/adjoint sweeps over all 2^n inputs; BDC_LITERAL: per-input
+ * subsequence enumeration and per-output supersequence enumeration on orbit
+ * representatives, Sec. 3-5 and Appendix A; FP64 only).  Iteration t uses p_t
+ * and q_t for its bounds; an instance stops after the iteration whose gap
+ * upper-lower is < gap_tol_bits (pass a negative value to never stop), and
+ * its p then holds the updated input.  lower/upper/iters_done are host
+ * arrays of nd (may be NULL): the bounds of the last iteration run and the
+ * iterations run by this call.  Iterations continue from the current p. */
+bdc_status bdc_ba_iterate(bdc_engine *eng, int max_iters, double gap_tol_bits, int precision, int impl,
+                          double *lower, double *upper, int *iters_done);
+
+/* Copy the per-iteration bound history of instance inst (the last
+ * min(len, 8192) iterations since bdc_bind or bdc_set_p) into host arrays;
+ * returns the number of entries written in *count. */
+bdc_status bdc_get_history(bdc_engine *eng, int inst, double *lower, double *upper, int len, int *count);
+
+/* D_x for every instance and every x, in double precision, into the caller's
+ * device array D_dev [nd][2^n].  q_dev NULL: q from the current p (computed
+ * in `precision`); otherwise q_dev is a device array [nd][2^(n+1)] of the
+ * given precision (float or double), indexed by code, any positive values
+ * (it is normalised internally: D uses q/sum q). */
+bdc_status bdc_divergence(bdc_engine *eng, const void *q_dev, int precision, double *D_dev);
+
+/* Certified upper bound on C_n(d) per instance, in FP64 with an explicit
+ * rounding-error margin (the dual bound max_x D(W_x || q/sum q) holds for
+ * every positive q).  q_dev NULL: q is the FP64 output marginal of the
+ * current p mixed with certify_mix of the uniform input; otherwise a device
+ * array [nd][2^(n+1)] of doubles (positive at every code).  Host arrays of
+ * nd: upper (the certified bound, rounded up), margin (the added rounding
+ * margin, bits), lower (FP64 Blahut lower bound of the current p; NaN when
+ * q_dev is given).  Any may be NULL. */
+bdc_status bdc_certify_upper(bdc_engine *eng, const double *q_dev, double *upper, double *margin, double *lower);
+
+/* --- state access (caller-owned host buffers, copied) -------------------- */
+
+/* p of every instance, normalised, host [nd][2^n]. */
+bdc_status bdc_get_p(bdc_engine *eng, double *p_host);
+/* Set p of every instance from host [nd][2^n] (non-negative, positive sum;
+ * normalised here).  Clears the bound history. */
+bdc_status bdc_set_p(bdc_engine *eng, const double *p_host);
+/* Output marginal q of the current p, host [nd][2^(n+1)] by code, computed in
+ * the given precision. */
+bdc_status bdc_get_q(bdc_engine *eng, int precision, double *q_host);
+/* d-free precompute of representative r (0 <= r < number of reps): its
+ * input string, orbit size, N_{x,k} and S_k for k = 0..n (host arrays of
+ * n+1). */
+bdc_status bdc_get_rep_stats(bdc_engine *eng, int64_t r, uint64_t *x, int *orbit, uint64_t *N_k, double *S_k);
+/* Number of orbit representatives of {0,1}^n. */
+int64_t bdc_num_reps(const bdc_engine *eng);
+/* Save / restore p and the iteration count to a file (binary). */
+bdc_status bdc_save(bdc_engine *eng, const char *path);
+bdc_status bdc_load(bdc_engine *eng, const char *path);
+
+/* --- smoothed dual bound and its adjoint ---------------------------------- */
+
+/* Number of output orbit classes (strings of every length up to n under
+ * complement and reversal, Appendix A). */
+int64_t bdc_num_output_classes(const bdc_engine *eng);
+/* Class index of every code, host int64 [2^(n+1)] (slot 0 = -1). */
+bdc_status bdc_output_classes(bdc_engine *eng, int64_t *cls_host);
+
+/* F = tau log2 sum_x 2^{D_x(q)/tau} for instance inst, with q the softmax of
+ * theta over output classes (theta_dev: device array of num_output_classes
+ * in `precision`).  Gradients (computed by forward and adjoint sweeps, never
+ * storing W): grad_theta_dev (device, same type and length as theta; may be
+ * NULL) and *grad_d = dF/dd at fixed theta (may be NULL; needs 0 < d < 1).
+ * *F and *max_D (max_x D_x, the bound itself) are host doubles. */
+bdc_status bdc_dual_bound(bdc_engine *eng, int inst, const void *theta_dev, double tau, int precision,
+                          double *F, double *max_D, void *grad_theta_dev, double *grad_d);
+
+/* --- measurement --------------------------------------------------------- */
+
+/* Number of kernels this engine has launched so far (kernels replayed inside
+ * CUDA graphs included). */
+int64_t bdc_launch_count(const bdc_engine *eng);
+
+/* Run `reps` iterations without graphs, recording a CUDA event on the bound
+ * stream after every stage (one kernel each), and return the mean time per
+ * stage in milliseconds (stage_ms, host array of >= 32), the stage names as
+ * a comma-separated list (names, host buffer of names_len bytes, may be
+ * NULL) and the number of stages.  The iterations are real BA iterations:
+ * they advance p like bdc_ba_iterate. */
+bdc_status bdc_profile_iteration(bdc_engine *eng, int precision, int impl, int reps, double *stage_ms, char *names,
+                                 int names_len, int *nstages);
+
+/* --- test hook ------------------------------------------------------------ */
+
+/* For nx inputs x_dev[i] (device uint64) of length n <= 32: per input and
+ * length k = 0..n the number of distinct subsequences (N_dev, device uint64
+ * [nx][n+1]) and S_k = sum count*log2(count) over them (S_dev, device double
+ * [nx][n+1], may be NULL); if nx == 1 and emb_dev != NULL, also the
+ * embedding count of every code (device uint64 [2^(n+1)], zero where y is
+ * not a subsequence).  Runs the same warp-cooperative enumeration as the
+ * precompute, on `stream`.  Synchronous. */
+bdc_status bdc_subseq_counts(int n, const uint64_t *x_dev, int64_t nx, uint64_t *N_dev, double *S_dev,
+                             uint64_t *emb_dev, void *cuda_stream);
+
+/* Thread-local message of the last failing call on this thread. */
+const char *bdc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BDC_H */

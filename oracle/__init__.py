@@ -70,6 +70,7 @@ def lib():
                 "orc_recsuperseq": (_u64, [_u64, _int, _int, _u64, _int]),
                 "orc_orbit_rep": (_u64, [_u64, _int, _P]),
                 "orc_dual_bound": (_dbl, [_int, _dbl, _dbl, _P, _P, _i64, _P, _P]),
+                "orc_D_list": (_i64, [_int, _dbl, _P, _P, _i64, _P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -147,6 +148,15 @@ def D_full(n: int, d: float, q: np.ndarray) -> np.ndarray:
     D = np.zeros(1 << n, np.float64)
     lib().orc_D_full(n, float(d), _ptr(q), _ptr(D))
     return D
+
+
+def D_list(n: int, d: float, q: np.ndarray, xs: np.ndarray):
+    """D_x for the given inputs (OpenMP); returns (D, pairs enumerated)."""
+    q = np.ascontiguousarray(q, np.float64)
+    xs = np.ascontiguousarray(xs, np.uint64)
+    D = np.zeros(len(xs), np.float64)
+    pairs = lib().orc_D_list(n, float(d), _ptr(q), _ptr(xs), len(xs), _ptr(D))
+    return D, int(pairs)
 
 
 def certify(n: int, d: float, q: np.ndarray):

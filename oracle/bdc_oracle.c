@@ -220,6 +220,18 @@ void orc_D_full(int n, double d, const double *q, double *D) {
     for (int64_t x = 0; x < nx; x++) D[x] = orc_D_point(n, d, q, (uint64_t)x);
 }
 
+/* D_x for a list of inputs (OpenMP over the list); returns the number of
+ * (x, distinct y) pairs enumerated.  Used to time the oracle on a sample. */
+int64_t orc_D_list(int n, double d, const double *q, const uint64_t *xs, int64_t count, double *D) {
+    int64_t pairs = 0;
+#pragma omp parallel for schedule(dynamic, 4) reduction(+ : pairs)
+    for (int64_t i = 0; i < count; i++) {
+        D[i] = orc_D_point(n, d, q, xs[i]);
+        pairs += orc_subseq_list(n, xs[i], NULL, NULL) + 1;
+    }
+    return pairs;
+}
+
 /* Dual (minimax) upper bound for any positive q: max_x D(W_x || q/sum q)
  * = max_x D_x(q) + log2 sum_y q(y).  Also returns argmax. */
 double orc_certify(int n, double d, const double *q, int64_t *argmax) {

@@ -1,0 +1,247 @@
+// Internal declarations shared by the CUDA translation units of libbdc.
+//
+// Encoding used throughout (paper Sec. 2.1 indexes strings from 0):
+//   x in {0,1}^n is the integer with x_0 as its most significant of n bits;
+//   an output y of length k has code (1<<k)|y; slot 0 of code arrays unused.
+//
+// Sweep index: at level i of a left-to-right pass over the input symbols, the
+// pair (u, s) -- u the output produced by x_0..x_{i-1}, s = x_i..x_{n-1} still
+// pending -- sits at P = (code(u) << (n-i)) | s.  Every level shares the index
+// range [1, 2^(n+1)); the number of deletions so far is delta(P) =
+// n + 1 - bitlen(P), independent of the level.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/bdc.h"
+
+#define BDC_MAXN 26
+#define BDC_HIST 8192
+
+// ---------------------------------------------------------------------------
+// error plumbing
+// ---------------------------------------------------------------------------
+void bdc_set_error(const std::string &msg);
+
+#define BDC_CUDA_TRY(call)                                                              \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            bdc_set_error(std::string(#call) + ": " + cudaGetErrorString(e_));          \
+            return BDC_ECUDA;                                                           \
+        }                                                                               \
+    } while (0)
+
+#define BDC_TRY(call)                                                                   \
+    do {                                                                                \
+        bdc_status s_ = (call);                                                         \
+        if (s_ != BDC_OK) return s_;                                                    \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// per-instance device scalars (double slots of inst[z * INST_STRIDE + .])
+// ---------------------------------------------------------------------------
+enum {
+    I_ACTIVE = 0,     // 1 while the instance iterates; 0 once its gap < tol
+    I_PENDING = 1,    // 1 when p must still be multiplied by 2^{Dbar - SHIFT}
+    I_SHIFT = 2,      // log2 of the last Z (the BA normalisation)
+    I_LOWER = 3,      // bounds of the last iteration
+    I_UPPER = 4,
+    I_ZP = 5,         // sum of unnormalised p of the last iteration
+    I_TOL = 6,        // gap tolerance for this call
+    I_ITERS = 7,      // iterations run in the current call
+    I_HISTN = 8,      // total iterations recorded in the history ring
+    I_STATUS = 9,     // 0 ok, else a bdc_status (non-finite, ...)
+    I_MAXD = 10,      // max_x D_stored of the last iteration
+    I_CERT_U = 11,    // certified bound
+    I_CERT_M = 12,    // its margin
+    I_CERT_LO = 13,   // FP64 lower bound of the certified input
+    I_LOG2SQ = 14,    // log2 sum q~ (certify)
+    I_LOG2SQ_ERR = 15,
+    I_EH = 16,        // certified bound on |Hb^ - Hb|
+    I_DUAL_F = 17,
+    I_DUAL_MAXD = 18,
+    I_DUAL_GD = 19,
+    I_DUAL_ZT = 20,   // log-sum-exp of theta over codes
+    I_SUMP = 21,
+    I_SYMNEED = 22,   // D of the last iteration still needs the orbit mean
+    I_NEGH = 23,      // sum_k b_k log2 b_k = -h(b): the length entropy, added when q is a full marginal
+    I_DUAL_S = 24,    // sum_x 2^{(D_x - max D)/tau}
+    I_DUAL_C0 = 25,   // sum_k rho_k b_k log2 b_k, rho_k = (n-k)/d - k/(1-d)
+    I_DUAL_TAU = 26,
+    INST_STRIDE = 32
+};
+
+// ---------------------------------------------------------------------------
+// sweep schedule: x = x1 x2 with |x1| = n1 (columns pass) and |x2| = n2 (rows
+// pass); n2 == 0 means a single in-CTA pass over all n symbols.
+// ---------------------------------------------------------------------------
+struct Sched {
+    int n1, n2, lw;  // lw = log2 of the column tile width
+    int nblk_cols;   // CTAs per instance of the columns passes
+};
+
+template <typename T>
+struct PrecBuf {
+    T *p;        // [nd][2^n] unnormalised input distribution
+    T *D;        // [nd][2^n] D_x - log2(sum p) of the last iteration (Dbar after symmetrising)
+    T *Hb;       // [nd][2^n] sum_k b_k H_k(x)
+    T *q;        // [nd][2^(n+1)] q_k(y) = sum_x p(x) Count(y,x) / C(n,k)
+    T *L;        // [nd][2^(n+1)] log2 q_k
+    T *F1;       // [nd][2^n1 rows][2^n2]   columns-pass output (rows >= 1)
+    T *Tm;       // [nd][2^(n1+1)][2^n2]     rows-pass output, codes c2 in [32, 2^n2)
+    T *Ts;       // [nd][32][2^(n1+1)]       rows-pass output, codes c2 < 32 (transposed)
+    T *Gb;       // [nd][2^(n1+1)][2^n2]     adjoint rows-pass output
+    double *part;  // [nd][2][maxblk][4] block partials
+    T *omega;    // [nd][n+1] weight applied to L in the adjoint: b_k / C(n,k)
+    T *aux;      // [nd][2^(n+1)] spare code-indexed array (dual bound, certify)
+    T *pd;       // [nd][2^n] spare input-indexed array (softmax weights of the dual bound)
+    T *omega2;   // [nd][n+1] rho_k b_k / C(n,k) (d-derivative of the adjoint weights)
+    Sched s;
+};
+
+struct bdc_engine {
+    int n = 0, nd = 0;
+    std::vector<double> d;
+    bdc_options opt;
+    size_t ws_bytes = 0;
+    char *ws = nullptr;
+    cudaStream_t stream = nullptr;
+    bool bound = false;
+
+    // d-free precompute
+    int64_t R = 0;          // number of input orbit representatives
+    int64_t Rout = 0;       // number of output orbit classes (all lengths)
+    uint32_t *reps = nullptr;   // [R] sorted
+    uint8_t *osize = nullptr;   // [R]
+    uint32_t *Nk = nullptr;     // [R][n+1]
+    double *Sk = nullptr;       // [R][n+1]
+    uint32_t *oreps = nullptr;  // [Rout] output class representative codes (sorted)
+    int32_t *ocls = nullptr;    // [2^(n+1)] code -> class index
+    uint32_t *counter = nullptr;  // work counters (16 words)
+    uint32_t *scan_tmp = nullptr; // block counts for compaction
+    double *bk = nullptr;       // [nd][n+1] b_k (FP64, host-exact)
+    double *tab_clog = nullptr; // [4096] c*log2(c)
+    double *inst = nullptr;     // [nd][INST_STRIDE]
+    double *hist = nullptr;     // [nd][2][BDC_HIST]
+    double *lit_part = nullptr; // literal path partial buffer
+    double *lit_q = nullptr;    // [nd][2^(n+1)] literal q (FP64)
+    double *lit_L = nullptr;
+    double *lit_p = nullptr;    // [nd][2^n] literal-path p (expanded over all x)
+    double *lit_D = nullptr;    // [nd][R]
+    double *pcert = nullptr;    // [nd][2^n] certify input
+    double *marg = nullptr;     // [nd][2^n] spare FP64 array (certify margins / D output)
+    double *dual_w = nullptr;   // [nd][n+1] rho_k b_k
+    uint64_t max_N = 0;         // max over reps and k of N_{x,k}
+
+    PrecBuf<float> f32;
+    PrecBuf<double> f64;
+
+    // graph cache per (precision, impl)
+    cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    int cur = 0;                // representation holding the current p: 0 FP32, 1 FP64, 2 literal
+    int64_t iters_total = 0;
+    int64_t launches = 0;       // kernels launched so far (graph replays included)
+    int64_t graph_kernels[2][2] = {{0, 0}, {0, 0}};
+    // stage profiling: when prof_n >= 0, each stage boundary records an event
+    cudaEvent_t prof_ev[32];
+    const char *prof_name[32];
+    bool prof_created = false;
+    int prof_n = -1;
+};
+
+// ---------------------------------------------------------------------------
+// host helpers
+// ---------------------------------------------------------------------------
+Sched make_sched(int n, int elem_bytes, int n2_override, int w_override);
+double binom_d(int n, int k);
+int64_t num_reps_host(int n);
+
+// enumeration (enum.cu)
+bdc_status launch_reps(bdc_engine *e);
+bdc_status launch_subseq_stats(bdc_engine *e);
+bdc_status launch_output_classes(bdc_engine *e);
+bdc_status launch_literal_q(bdc_engine *e);
+bdc_status launch_literal_D(bdc_engine *e);
+
+// sweep (sweep.cu)
+template <typename T>
+bdc_status sweep_prepare(bdc_engine *e, PrecBuf<T> &b);
+template <typename T>
+bdc_status sweep_forward(bdc_engine *e, PrecBuf<T> &b, const T *p_src, int apply_update, int mode);
+template <typename T>
+bdc_status sweep_adjoint(bdc_engine *e, PrecBuf<T> &b, const T *Lsrc, const T *omega, T *Dout, int mode);
+
+// BA glue (ba.cu)
+template <typename T>
+bdc_status launch_build_Hb(bdc_engine *e, PrecBuf<T> &b);
+bdc_status launch_build_Hb_w(bdc_engine *e, const double *w, double *out);
+template <typename T>
+bdc_status launch_finalize(bdc_engine *e, PrecBuf<T> &b, int mode, int add_negh = 0);
+template <typename T>
+bdc_status launch_symmetrize(bdc_engine *e, T *D);
+template <typename T>
+bdc_status launch_apply_pending(bdc_engine *e, PrecBuf<T> &b);
+bdc_status launch_literal_update(bdc_engine *e);
+bdc_status launch_literal_reduce(bdc_engine *e);
+bdc_status launch_clear_pending(bdc_engine *e);
+bdc_status launch_finalize_literal(bdc_engine *e, int nblk0, int nblk1);
+bdc_status launch_expand_reps(bdc_engine *e, const double *Dr, double *out);
+int literal_grid(const bdc_engine *e);
+int part_maxblk(const bdc_engine *e);
+int64_t literal_items(int n);
+size_t literal_part_bytes(int n, int nd);
+bdc_status upload_literal_tables(bdc_engine *e);
+bdc_status subseq_counts_impl(int n, const uint64_t *x_dev, int64_t nx, uint64_t *N_dev, double *S_dev,
+                              uint64_t *emb_dev, cudaStream_t st, const double *tab_clog);
+
+// record a stage boundary when profiling (no-op otherwise)
+inline void stage_mark(bdc_engine *e, const char *name) {
+    if (e->prof_n >= 0 && e->prof_n < 32) {
+        e->prof_name[e->prof_n] = name;
+        cudaEventRecord(e->prof_ev[e->prof_n++], e->stream);
+    }
+}
+
+// modes of the sweep epilogues
+enum { MODE_ITER = 0, MODE_CERT = 1, MODE_DIV = 2, MODE_DUAL = 3, MODE_DUAL_D = 4 };
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int bitlen32(uint32_t v) { return 32 - __clz(v); }
+
+__device__ __forceinline__ uint32_t rev_bits(uint32_t v, int L) {
+    return L == 0 ? 0u : (__brev(v) >> (32 - L));
+}
+
+// smallest member of the orbit of s (length L) under complement and reversal
+__device__ __forceinline__ uint32_t orbit_rep_dev(uint32_t s, int L, int *osize) {
+    uint32_t mask = (L >= 32) ? 0xffffffffu : ((1u << L) - 1u);
+    uint32_t a = s, b = s ^ mask, c = rev_bits(s, L), dd = c ^ mask;
+    uint32_t m = min(min(a, b), min(c, dd));
+    if (osize) {
+        int cnt = 1;
+        if (b != a) cnt++;
+        if (c != a && c != b) cnt++;
+        if (dd != a && dd != b && dd != c) cnt++;
+        *osize = cnt;
+    }
+    return m;
+}
+
+template <typename T>
+__device__ __forceinline__ T log2_t(T v);
+template <>
+__device__ __forceinline__ float log2_t<float>(float v) { return __log2f(v); }
+template <>
+__device__ __forceinline__ double log2_t<double>(double v) { return log2(v); }
+
+template <typename T>
+__device__ __forceinline__ T exp2_t(T v);
+template <>
+__device__ __forceinline__ float exp2_t<float>(float v) { return exp2f(v); }
+template <>
+__device__ __forceinline__ double exp2_t<double>(double v) { return exp2(v); }

@@ -1,0 +1,608 @@
+// Enumeration kernels: orbit representatives (Appendix A), the
+// warp-cooperative walk over the distinct subsequences of an input (Sec. 4:
+// N_{x,k}, embedding multiplicities, S_k = sum count*log2 count, and the
+// literal per-input divergence of Sec. 3), and the walk over the
+// supersequences of an output (Sec. 5: the literal output marginal).
+//
+// Warp-cooperative subsequence walk.  Lane j holds position j of x.  A trie
+// node y carries E_j = #embeddings of y into x whose last symbol sits at x_j.
+// With S_j = sum_{j'<j} E_{j'} (exclusive warp scan; S_j = 1 at the root),
+// the child y.b has E'_j = [x_j = b] S_j and Count(y.b, x) = sum_j E'_j; the
+// child exists (y.b is a subsequence) iff that count is > 0.  This is the
+// embedding-count form of the paper's NextPos/Cnt recursion: the lowest lane
+// with E'_j > 0 is NextPos of the parent's first embedding, and the walk
+// visits the distinct subsequences in lexicographic (unrank) order.
+#include "bdc_internal.cuh"
+
+#include <algorithm>
+#include <cstring>
+
+namespace {
+
+constexpr int WARPS_PER_CTA = 8;
+constexpr int STK = 28;  // >= BDC_MAXN + 2
+
+__device__ __forceinline__ uint32_t warp_excl_scan(uint32_t v, int lane) {
+    uint32_t s = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= o) s += t;
+    }
+    return s - v;
+}
+
+__device__ __forceinline__ double clog2c(uint32_t c, const double *__restrict__ tab) {
+    if (tab != nullptr && c < 4096u) return __ldg(tab + c);
+    return c <= 1u ? 0.0 : (double)c * log2((double)c);
+}
+
+// ---------------------------------------------------------------------------
+// orbit representatives of {0,1}^L (L = n for inputs) : is_rep flags counted
+// per block, scanned, then written in increasing order (deterministic).
+// ---------------------------------------------------------------------------
+constexpr int COMPACT_THREADS = 256;
+constexpr int COMPACT_PER_THREAD = 8;
+constexpr int COMPACT_TILE = COMPACT_THREADS * COMPACT_PER_THREAD;
+
+// mode 0: inputs of length n (code space x in [0,2^n)); mode 1: output codes
+// c in [1, 2^(n+1)) (string of length bitlen(c)-1).
+__device__ __forceinline__ bool is_rep_item(uint32_t v, int n, int mode) {
+    if (mode == 0) return orbit_rep_dev(v, n, nullptr) == v;
+    if (v == 0) return false;
+    int k = bitlen32(v) - 1;
+    uint32_t y = v ^ (1u << k);
+    return orbit_rep_dev(y, k, nullptr) == y;
+}
+
+__global__ void k_count_reps(int n, int mode, uint64_t total, uint32_t *blk_counts) {
+    __shared__ uint32_t red[COMPACT_THREADS / 32];
+    uint64_t base = (uint64_t)blockIdx.x * COMPACT_TILE;
+    uint32_t c = 0;
+    for (int i = 0; i < COMPACT_PER_THREAD; i++) {
+        uint64_t v = base + (uint64_t)i * COMPACT_THREADS + threadIdx.x;
+        if (v < total && is_rep_item((uint32_t)v, n, mode)) c++;
+    }
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t s = 0;
+        for (int w = 0; w < COMPACT_THREADS / 32; w++) s += red[w];
+        blk_counts[blockIdx.x] = s;
+    }
+}
+
+// single-block exclusive scan of nb block counts (sequential per thread chunk)
+__global__ void k_scan_counts(uint32_t *cnt, int nb) {
+    __shared__ uint32_t part[1024];
+    int per = (nb + blockDim.x - 1) / blockDim.x;
+    int lo = threadIdx.x * per, hi = min(nb, lo + per);
+    uint32_t s = 0;
+    for (int i = lo; i < hi; i++) s += cnt[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int t = 0; t < (int)blockDim.x; t++) {
+            uint32_t v = part[t];
+            part[t] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+    uint32_t run = part[threadIdx.x];
+    for (int i = lo; i < hi; i++) {
+        uint32_t v = cnt[i];
+        cnt[i] = run;
+        run += v;
+    }
+}
+
+__global__ void k_write_reps(int n, int mode, uint64_t total, const uint32_t *blk_off, uint32_t *out,
+                             uint8_t *osize, int32_t *cls) {
+    __shared__ uint32_t wsum[COMPACT_THREADS / 32];
+    uint64_t base = (uint64_t)blockIdx.x * COMPACT_TILE;
+    uint32_t run = blk_off[blockIdx.x];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int i = 0; i < COMPACT_PER_THREAD; i++) {
+        uint64_t v = base + (uint64_t)i * COMPACT_THREADS + threadIdx.x;
+        bool f = v < total && is_rep_item((uint32_t)v, n, mode);
+        uint32_t bal = __ballot_sync(0xffffffffu, f);
+        uint32_t before = __popc(bal & ((1u << lane) - 1u));
+        if (lane == 0) wsum[wid] = __popc(bal);
+        __syncthreads();
+        uint32_t woff = 0, tot = 0;
+        for (int w = 0; w < COMPACT_THREADS / 32; w++) {
+            if (w < wid) woff += wsum[w];
+            tot += wsum[w];
+        }
+        if (f) {
+            uint32_t idx = run + woff + before;
+            out[idx] = (uint32_t)v;
+            if (mode == 0) {
+                int o;
+                orbit_rep_dev((uint32_t)v, n, &o);
+                osize[idx] = (uint8_t)o;
+            } else {
+                cls[v] = (int32_t)idx;
+            }
+        }
+        run += tot;
+        __syncthreads();
+    }
+}
+
+// every output code gets the class index of its representative
+__global__ void k_fill_classes(int n, int32_t *cls) {
+    uint64_t total = 1ull << (n + 1);
+    for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < total;
+         c += (uint64_t)gridDim.x * blockDim.x) {
+        if (c == 0) { cls[0] = -1; continue; }
+        int k = bitlen32((uint32_t)c) - 1;
+        uint32_t y = (uint32_t)c ^ (1u << k);
+        uint32_t r = orbit_rep_dev(y, k, nullptr);
+        if (r != y) cls[c] = cls[(1u << k) | r];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// subsequence walk
+// ---------------------------------------------------------------------------
+enum { WALK_STATS = 0, WALK_LITERAL_D = 1, WALK_EMIT = 2 };
+
+struct WalkArgs {
+    int n;
+    int64_t count;              // number of inputs to process
+    const uint32_t *xs32;       // inputs (reps) as uint32, or
+    const uint64_t *xs64;       // inputs as uint64 (test hook)
+    uint32_t *counter;          // dynamic work counter (may be null: static)
+    // WALK_STATS
+    uint32_t *Nk32; uint64_t *Nk64; double *Sk; int stride;
+    const double *tab;          // c*log2(c) for c < 4096
+    const double *tab_log2;     // log2(c) for c < 4096
+    // WALK_LITERAL_D
+    const double *L;            // [nd][2^(n+1)] log2 q_k
+    const double *kw;           // [nd][n+1] d^(n-k)(1-d)^k
+    const double *lkw;          // [nd][n+1] log2 of kw (or 0 where kw == 0)
+    const double *lb;           // [nd][n+1] log2 b_k
+    double *Dout;               // [nd][count]
+    const double *inst;
+    // WALK_EMIT
+    uint64_t *emb;
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) {
+    __shared__ uint32_t stkE[WARPS_PER_CTA][STK][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int n = a.n;
+    const int z = blockIdx.y;  // instance (literal D)
+    const unsigned FULL = 0xffffffffu;
+    if (MODE == WALK_LITERAL_D && a.inst[z * INST_STRIDE + I_ACTIVE] == 0.0) return;
+    const double *L = (MODE == WALK_LITERAL_D) ? a.L + ((size_t)z << (n + 1)) : nullptr;
+    const double *kw = (MODE == WALK_LITERAL_D) ? a.kw + z * (n + 1) : nullptr;
+    const double *lkw = (MODE == WALK_LITERAL_D) ? a.lkw + z * (n + 1) : nullptr;
+    const double *lb = (MODE == WALK_LITERAL_D) ? a.lb + z * (n + 1) : nullptr;
+    int64_t item = -1;
+    int64_t static_next = (int64_t)blockIdx.x * WARPS_PER_CTA + wid;
+    const int64_t static_stride = (int64_t)gridDim.x * WARPS_PER_CTA;
+    while (true) {
+        if (a.counter) {
+            uint32_t v = 0;
+            if (lane == 0) v = atomicAdd(a.counter + (MODE == WALK_LITERAL_D ? z : 0), 1u);
+            item = __shfl_sync(FULL, v, 0);
+        } else {
+            item = static_next;
+            static_next += static_stride;
+        }
+        if (item >= a.count) break;
+        uint64_t x = a.xs32 ? (uint64_t)a.xs32[item] : a.xs64[item];
+        const int xb = (lane < n) ? (int)((x >> (n - 1 - lane)) & 1u) : 2;
+        // per-lane accumulators: lane k owns length k (stats) / a 32-slot
+        // gather buffer (literal D)
+        uint32_t accN = (lane == 0) ? 1u : 0u;
+        double accS = 0.0;
+        double accD = 0.0;
+        uint32_t bcode = 0, bcnt = 0;
+        int nbuf = 0;
+        uint32_t stk_code = 0, stk_cnt = 0;  // lane s holds stack slot s
+        int sp = 0;
+        if (MODE == WALK_EMIT && lane == 0) a.emb[1] = 1;
+        if (MODE == WALK_LITERAL_D) {
+            // empty output: count 1, weight d^n
+            double w = kw[0];
+            if (lane == 0 && w > 0.0) accD += w * (lkw[0] - lb[0] - L[1]);
+        }
+        // root children
+#pragma unroll
+        for (int b = 1; b >= 0; b--) {
+            uint32_t E = (xb == b) ? 1u : 0u;
+            uint32_t c = __popc(__ballot_sync(FULL, xb == b));
+            if (c > 0) {
+                stkE[wid][sp][lane] = E;
+                if (lane == sp) { stk_code = 2u | (uint32_t)b; stk_cnt = c; }
+                sp++;
+            }
+        }
+        while (sp > 0) {
+            sp--;
+            uint32_t E = stkE[wid][sp][lane];
+            uint32_t code = __shfl_sync(FULL, stk_code, sp);
+            uint32_t cnt = __shfl_sync(FULL, stk_cnt, sp);
+            int k = bitlen32(code) - 1;
+            // record (code, k, cnt)
+            if (MODE == WALK_STATS) {
+                if (lane == k) { accN++; accS += clog2c(cnt, a.tab); }
+            } else if (MODE == WALK_EMIT) {
+                if (lane == 0) a.emb[code] = cnt;
+            } else {
+                if (lane == nbuf) { bcode = code; bcnt = cnt; }
+                nbuf++;
+                if (nbuf == 32) {
+                    int kk = bitlen32(bcode) - 1;
+                    double w = (double)bcnt * kw[kk];
+                    if (w > 0.0) {
+                        double lc = bcnt < 4096u ? __ldg(a.tab_log2 + bcnt) : log2((double)bcnt);
+                        accD += w * (lc + lkw[kk] - lb[kk] - L[bcode]);
+                    }
+                    nbuf = 0;
+                }
+            }
+            if (k == n) continue;
+            uint32_t S = warp_excl_scan(E, lane);
+#pragma unroll
+            for (int b = 1; b >= 0; b--) {
+                uint32_t Eb = (xb == b) ? S : 0u;
+                uint32_t cb = __reduce_add_sync(FULL, Eb);
+                if (cb > 0) {
+                    stkE[wid][sp][lane] = Eb;
+                    if (lane == sp) { stk_code = (code << 1) | (uint32_t)b; stk_cnt = cb; }
+                    sp++;
+                }
+            }
+        }
+        if (MODE == WALK_STATS) {
+            if (lane <= n) {
+                if (a.Nk32) a.Nk32[item * a.stride + lane] = accN;
+                if (a.Nk64) a.Nk64[item * a.stride + lane] = accN;
+                if (a.Sk) a.Sk[item * a.stride + lane] = accS;
+            }
+        } else if (MODE == WALK_LITERAL_D) {
+            if (lane < nbuf) {
+                int kk = bitlen32(bcode) - 1;
+                double w = (double)bcnt * kw[kk];
+                if (w > 0.0) {
+                    double lc = bcnt < 4096u ? __ldg(a.tab_log2 + bcnt) : log2((double)bcnt);
+                    accD += w * (lc + lkw[kk] - lb[kk] - L[bcode]);
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) accD += __shfl_xor_sync(FULL, accD, o);
+            if (lane == 0) a.Dout[(size_t)z * a.count + item] = accD;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// supersequence walk (literal output marginal).  Work item = (output class
+// representative y of length k, first s_k symbols of x).  Lane j in [0, k]
+// holds M_j = #embeddings of y_0..y_{j-1} into the current prefix of x
+// (M_0 = 1); appending symbol b gives M'_j = M_j + [y_{j-1} = b] M_{j-1}.  A
+// prefix of length i stays only if its longest embedded prefix of y, m, has
+// m + (n - i) >= k (Lemma num_superseq's supersequences are exactly the
+// leaves).  Leaf x contributes p(x) * M_k.
+// ---------------------------------------------------------------------------
+struct SuperArgs {
+    int n;
+    int64_t nitems;
+    const uint32_t *oreps;      // class representative codes
+    const int64_t *koff;        // [n+2] first class index of each length
+    const int64_t *ioff;        // [n+2] first item index of each length
+    const int *ks;              // [n+1] split bits per length
+    const double *p;            // [nd][2^n]
+    double *part;               // [nd][nitems]
+    const double *inst;
+};
+
+__global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_super_walk(SuperArgs a, uint32_t *counter) {
+    __shared__ uint32_t stkM[WARPS_PER_CTA][STK][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned FULL = 0xffffffffu;
+    const int n = a.n;
+    const int z = blockIdx.y;
+    if (a.inst[z * INST_STRIDE + I_ACTIVE] == 0.0) return;
+    const double *p = a.p + ((size_t)z << n);
+    while (true) {
+        uint32_t v = 0;
+        if (lane == 0) v = atomicAdd(counter + z, 1u);
+        int64_t item = __shfl_sync(FULL, v, 0);
+        if (item >= a.nitems) break;
+        int k = 0;
+        while (k < n && a.ioff[k + 1] <= item) k++;
+        int s = a.ks[k];
+        int64_t rel = item - a.ioff[k];
+        int64_t cls = a.koff[k] + (rel >> s);
+        uint32_t prefix = (uint32_t)(rel & ((1ll << s) - 1));
+        uint32_t code = a.oreps[cls];
+        uint32_t y = code ^ (1u << k);
+        // lane j >= 1 matches y_{j-1}
+        int ysym = (lane >= 1 && lane <= k) ? (int)((y >> (k - lane)) & 1u) : 2;
+        uint32_t M = (lane == 0) ? 1u : 0u;
+        bool alive = true;
+        for (int i = 0; i < s; i++) {
+            int b = (prefix >> (s - 1 - i)) & 1;
+            uint32_t up = __shfl_up_sync(FULL, M, 1);
+            if (ysym == b) M += up;
+            uint32_t bal = __ballot_sync(FULL, M > 0u && lane <= k);
+            int m = 31 - __clz(bal);
+            if (m + (n - i - 1) < k) { alive = false; break; }
+        }
+        double acc = 0.0;
+        uint32_t bx = 0, bc = 0;
+        int nbuf = 0;
+        if (alive) {
+            // iterative walk from depth s; lane t holds the next child to try
+            // at depth t, stkM[t] the embedding vector of the prefix of length t
+            int depth = s;
+            uint32_t x = prefix;
+            uint32_t nb_lane = 0;
+            stkM[wid][depth][lane] = M;
+            while (true) {
+                if (depth == n) {
+                    uint32_t cnt = __shfl_sync(FULL, M, k);
+                    if (lane == nbuf) { bx = x; bc = cnt; }
+                    nbuf++;
+                    if (nbuf == 32) {
+                        acc += p[bx] * (double)bc;
+                        nbuf = 0;
+                    }
+                    depth--;
+                    x >>= 1;
+                    if (depth < s) break;
+                    M = stkM[wid][depth][lane];
+                    continue;
+                }
+                int b = (int)__shfl_sync(FULL, nb_lane, depth);
+                if (b > 1) {
+                    depth--;
+                    x >>= 1;
+                    if (depth < s) break;
+                    M = stkM[wid][depth][lane];
+                    continue;
+                }
+                if (lane == depth) nb_lane = (uint32_t)(b + 1);
+                uint32_t up = __shfl_up_sync(FULL, M, 1);
+                uint32_t Mc = M + ((ysym == b) ? up : 0u);
+                uint32_t bal = __ballot_sync(FULL, Mc > 0u && lane <= k);
+                int m = 31 - __clz(bal);
+                if (m + (n - depth - 1) < k) continue;  // not completable: prune
+                depth++;
+                x = (x << 1) | (uint32_t)b;
+                M = Mc;
+                if (depth < n) {
+                    stkM[wid][depth][lane] = M;
+                    if (lane == depth) nb_lane = 0;
+                }
+            }
+        }
+        if (lane < nbuf) acc += p[bx] * (double)bc;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+        if (lane == 0) a.part[(size_t)z * a.nitems + item] = acc;
+    }
+}
+
+// sum the items of every class in order, normalise by C(n,k), write q and
+// log2 q to every code of the orbit
+__global__ void k_super_reduce(int n, int64_t Rout, const uint32_t *oreps, const int64_t *ioff,
+                               const int64_t *koff, const int *ks, const double *part, int64_t nitems,
+                               const double *inv_binom, double *q, double *Lq, const double *inst) {
+    const int z = blockIdx.y;
+    if (inst[z * INST_STRIDE + I_ACTIVE] == 0.0) return;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < Rout;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t code = oreps[r];
+        int k = bitlen32(code) - 1;
+        int s = ks[k];
+        int64_t first = ioff[k] + ((r - koff[k]) << s);
+        double acc = 0.0;
+        for (int64_t t = 0; t < (1ll << s); t++) acc += part[(size_t)z * nitems + first + t];
+        double qv = acc * inv_binom[k];
+        double lv = log2(qv);
+        uint32_t y = code ^ (1u << k);
+        uint32_t mask = k ? ((1u << k) - 1u) : 0u;
+        uint32_t ry = rev_bits(y, k);
+        uint32_t mem[4] = {y, y ^ mask, ry, ry ^ mask};
+        double *qz = q + ((size_t)z << (n + 1));
+        double *lz = Lq + ((size_t)z << (n + 1));
+        for (int t = 0; t < 4; t++) {
+            uint32_t c = (1u << k) | mem[t];
+            qz[c] = qv;
+            lz[c] = lv;
+        }
+    }
+}
+
+int64_t count_items_host(int n, const std::vector<int64_t> &Rk, std::vector<int> &ks, std::vector<int64_t> &ioff) {
+    ks.assign(n + 1, 0);
+    ioff.assign(n + 2, 0);
+    for (int k = 0; k <= n; k++) {
+        double leaves = 0;
+        for (int i = 0; i <= n - k; i++) leaves += binom_d(n, i);
+        int s = 0;
+        while (s < n - k && leaves / (double)(1ll << s) > 4096.0) s++;
+        ks[k] = s;
+        ioff[k + 1] = ioff[k] + (Rk[k] << s);
+    }
+    return ioff[n + 1];
+}
+
+}  // namespace
+
+// number of orbit reps of {0,1}^L (Burnside over {id, cpl, rev, cpl rev})
+int64_t num_reps_host(int L) {
+    if (L == 0) return 1;
+    int64_t fix_rev = 1ll << ((L + 1) / 2);
+    int64_t fix_crev = (L % 2 == 0) ? (1ll << (L / 2)) : 0;
+    return ((1ll << L) + fix_rev + fix_crev) / 4;
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static bdc_status compact(bdc_engine *e, int mode, uint32_t *out, uint8_t *osize, int32_t *cls) {
+    uint64_t total = (mode == 0) ? (1ull << e->n) : (1ull << (e->n + 1));
+    int nb = (int)((total + COMPACT_TILE - 1) / COMPACT_TILE);
+    k_count_reps<<<nb, COMPACT_THREADS, 0, e->stream>>>(e->n, mode, total, e->scan_tmp); e->launches++;
+    k_scan_counts<<<1, 1024, 0, e->stream>>>(e->scan_tmp, nb); e->launches++;
+    k_write_reps<<<nb, COMPACT_THREADS, 0, e->stream>>>(e->n, mode, total, e->scan_tmp, out, osize, cls); e->launches++;
+    BDC_CUDA_TRY(cudaGetLastError());
+    return BDC_OK;
+}
+
+bdc_status launch_reps(bdc_engine *e) { return compact(e, 0, e->reps, e->osize, nullptr); }
+
+bdc_status launch_output_classes(bdc_engine *e) {
+    BDC_TRY(compact(e, 1, e->oreps, nullptr, e->ocls));
+    k_fill_classes<<<1024, 256, 0, e->stream>>>(e->n, e->ocls); e->launches++;
+    BDC_CUDA_TRY(cudaGetLastError());
+    return BDC_OK;
+}
+
+static int walk_grid() {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms * 8;
+}
+
+bdc_status launch_subseq_stats(bdc_engine *e) {
+    WalkArgs a{};
+    a.n = e->n;
+    a.count = e->R;
+    a.xs32 = e->reps;
+    a.counter = e->counter;
+    a.Nk32 = e->Nk;
+    a.Sk = e->Sk;
+    a.stride = e->n + 1;
+    a.tab = e->tab_clog;
+    BDC_CUDA_TRY(cudaMemsetAsync(e->counter, 0, 64 * sizeof(uint32_t), e->stream));
+    k_subseq_walk<WALK_STATS><<<walk_grid(), WARPS_PER_CTA * 32, 0, e->stream>>>(a); e->launches++;
+    BDC_CUDA_TRY(cudaGetLastError());
+    return BDC_OK;
+}
+
+// literal D on representatives: Dout[z][r] = sum_y W log2(W / (b_k q_k(y)))
+bdc_status launch_literal_D(bdc_engine *e) {
+    WalkArgs a{};
+    a.n = e->n;
+    a.count = e->R;
+    a.xs32 = e->reps;
+    a.counter = e->counter + 64;
+    a.tab_log2 = e->tab_clog + 4096;
+    a.L = e->lit_L;
+    a.kw = e->bk + (size_t)e->nd * (e->n + 1);
+    a.lkw = e->bk + (size_t)2 * e->nd * (e->n + 1);
+    a.lb = e->bk + (size_t)3 * e->nd * (e->n + 1);
+    a.Dout = e->lit_D;
+    a.inst = e->inst;
+    BDC_CUDA_TRY(cudaMemsetAsync(e->counter + 64, 0, e->nd * sizeof(uint32_t), e->stream));
+    dim3 grid(walk_grid() / 2 > 1 ? walk_grid() / 2 : 1, e->nd);
+    k_subseq_walk<WALK_LITERAL_D><<<grid, WARPS_PER_CTA * 32, 0, e->stream>>>(a); e->launches++; stage_mark(e, "literal_D_walk");
+    BDC_CUDA_TRY(cudaGetLastError());
+    return BDC_OK;
+}
+
+// literal q: item tables live in the literal partial buffer header
+struct SuperTables {
+    std::vector<int64_t> koff, ioff;
+    std::vector<int> ks;
+    int64_t nitems;
+};
+
+static SuperTables super_tables(int n) {
+    SuperTables t;
+    std::vector<int64_t> Rk(n + 1);
+    for (int k = 0; k <= n; k++) Rk[k] = num_reps_host(k);
+    t.koff.assign(n + 2, 0);
+    for (int k = 0; k <= n; k++) t.koff[k + 1] = t.koff[k] + Rk[k];
+    t.nitems = count_items_host(n, Rk, t.ks, t.ioff);
+    return t;
+}
+
+int64_t literal_items(int n) { return super_tables(n).nitems; }
+
+// device-side item tables, at the start of the literal partial buffer
+struct LitTab {
+    int64_t koff[BDC_MAXN + 2];
+    int64_t ioff[BDC_MAXN + 2];
+    int ks[BDC_MAXN + 2];
+    double inv_binom[BDC_MAXN + 2];
+};
+size_t literal_part_bytes(int n, int nd) {
+    return ((sizeof(LitTab) + 255) & ~(size_t)255) + (size_t)nd * (size_t)literal_items(n) * sizeof(double);
+}
+
+bdc_status upload_literal_tables(bdc_engine *e) {
+    const int n = e->n;
+    SuperTables t = super_tables(n);
+    LitTab h;
+    memset(&h, 0, sizeof h);
+    for (int k = 0; k <= n + 1; k++) { h.koff[k] = t.koff[k]; h.ioff[k] = t.ioff[k]; }
+    for (int k = 0; k <= n; k++) { h.ks[k] = t.ks[k]; h.inv_binom[k] = 1.0 / binom_d(n, k); }
+    BDC_CUDA_TRY(cudaMemcpy(e->lit_part, &h, sizeof h, cudaMemcpyHostToDevice));
+    return BDC_OK;
+}
+
+bdc_status launch_literal_q(bdc_engine *e) {
+    const int n = e->n;
+    SuperTables t = super_tables(n);
+    LitTab *dt = (LitTab *)e->lit_part;
+    double *part = (double *)((char *)e->lit_part + ((sizeof(LitTab) + 255) & ~(size_t)255));
+    uint32_t *ctr = e->counter + 64 + e->nd;
+    BDC_CUDA_TRY(cudaMemsetAsync(ctr, 0, e->nd * sizeof(uint32_t), e->stream));
+    SuperArgs a{};
+    a.n = n;
+    a.nitems = t.nitems;
+    a.oreps = e->oreps;
+    a.koff = dt->koff;
+    a.ioff = dt->ioff;
+    a.ks = dt->ks;
+    a.p = e->lit_p;
+    a.part = part;
+    a.inst = e->inst;
+    dim3 grid(walk_grid() / 2 > 1 ? walk_grid() / 2 : 1, e->nd);
+    k_super_walk<<<grid, WARPS_PER_CTA * 32, 0, e->stream>>>(a, ctr); e->launches++; stage_mark(e, "literal_q_walk");
+    dim3 g2((unsigned)std::min<int64_t>((e->Rout + 255) / 256, 4096), e->nd);
+    k_super_reduce<<<g2, 256, 0, e->stream>>>(n, e->Rout, e->oreps, dt->ioff, dt->koff, dt->ks, part,
+                                              t.nitems, dt->inv_binom, e->lit_q, e->lit_L, e->inst); e->launches++; stage_mark(e, "literal_q_reduce");
+    BDC_CUDA_TRY(cudaGetLastError());
+    return BDC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// test hook
+// ---------------------------------------------------------------------------
+bdc_status subseq_counts_impl(int n, const uint64_t *x_dev, int64_t nx, uint64_t *N_dev, double *S_dev,
+                              uint64_t *emb_dev, cudaStream_t st, const double *tab_clog) {
+    WalkArgs a{};
+    a.n = n;
+    a.count = nx;
+    a.xs64 = x_dev;
+    a.Nk64 = N_dev;
+    a.Sk = S_dev;
+    a.stride = n + 1;
+    a.tab = tab_clog;
+    int grid = (int)std::min<int64_t>((nx + WARPS_PER_CTA - 1) / WARPS_PER_CTA, walk_grid());
+    if (grid < 1) grid = 1;
+    k_subseq_walk<WALK_STATS><<<grid, WARPS_PER_CTA * 32, 0, st>>>(a);
+    BDC_CUDA_TRY(cudaGetLastError());
+    if (emb_dev && nx == 1) {
+        BDC_CUDA_TRY(cudaMemsetAsync(emb_dev, 0, (size_t)sizeof(uint64_t) << (n + 1), st));
+        a.emb = emb_dev;
+        k_subseq_walk<WALK_EMIT><<<1, WARPS_PER_CTA * 32, 0, st>>>(a);
+        BDC_CUDA_TRY(cudaGetLastError());
+    }
+    return BDC_OK;
+}

@@ -1,0 +1,521 @@
+// Factorised output-marginal sweep and its adjoint.
+//
+// The channel is never stored.  Reading the input symbols left to right, the
+// count-weighted state F_i(u, s) = sum_{r in {0,1}^i} p(r s) Count(u, r) obeys
+// (Count of a string ending in symbol b either skips b or matches it with the
+// last symbol of u):
+//     F_{i+1}(u, s') = F_i(u, 0 s') + F_i(u, 1 s') + F_i(u^-, u_last s')
+// and F_n(y) = sum_x p(x) Count(y, x) = C(n,k) q_k(y), the output marginal of
+// the exact channel BDC_{n,k} (Sec. 2.2).  In the index P = code(u) << (n-i) | s
+// the last term is at P itself, so one step is
+//     out[P] = in[P] + in[ins0(P)] + in[ins1(P)]      (P < 2^n)
+//     out[P] = in[P]                                   (P >= 2^n, no deletion yet)
+// where ins_b(P) inserts bit b at position m = n-i-1.  The adjoint step is
+//     G_i[Q] = G_{i+1}[Q] + G_{i+1}[cmp(Q)],  cmp removes bit m.
+// Both are pure additions of same-sign terms (exact up to rounding).
+//
+// The input is split x = x1 x2 (|x1| = n1, |x2| = n2).  Count factorises over
+// the split: Count(y, x1 x2) = sum_{y = u1 u2} Count(u1, x1) Count(u2, x2), so
+//   pass 1 (columns): for every x2, the n1-symbol sweep over x1 -> F1[c1][x2]
+//   pass 2 (rows):    for every code c1, the n2-symbol sweep over x2 -> T[c1][c2]
+//   combine:          F_n(y) = sum over splits y = u1 u2 of T[code u1][code u2]
+// and the adjoint runs the transposes in reverse order (the combine's
+// transpose is a gather fused into the adjoint rows pass).  Each pass keeps
+// its whole tile in shared memory; global memory sees each value a few times
+// per iteration instead of once per symbol.
+#include "bdc_internal.cuh"
+
+#include <algorithm>
+
+namespace {
+
+constexpr int SW_THREADS = 512;
+constexpr int SW_R = 16;
+
+// forward sweep of nn symbols over a tile of (2 << nn) rows x (1 << lw)
+// columns held in shared memory (rows >= 2^nn hold the input, rows < 2^nn
+// start at zero).  Rows are updated in increasing order, chunk by chunk:
+// a row only reads rows >= itself, so one barrier per chunk is enough.
+template <typename T>
+__device__ void lsweep_fwd(T *buf, int nn, int lw) {
+    const int tid = threadIdx.x;
+    for (int i = 0; i < nn; i++) {
+        const int m = nn - i - 1;
+        const uint32_t row_lo = 1u << m;
+        const uint32_t nel = ((1u << nn) - row_lo) << lw;
+        const uint32_t cmask = (1u << lw) - 1u;
+        for (uint32_t base = 0; base < nel; base += SW_THREADS * SW_R) {
+            T v[SW_R];
+#pragma unroll
+            for (int r = 0; r < SW_R; r++) {
+                uint32_t e = base + r * SW_THREADS + tid;
+                if (e < nel) {
+                    uint32_t P = row_lo + (e >> lw);
+                    uint32_t c = e & cmask;
+                    uint32_t i0 = ((P >> m) << (m + 1)) | (P & (row_lo - 1u));
+                    v[r] = buf[(P << lw) | c] + buf[(i0 << lw) | c] + buf[((i0 | row_lo) << lw) | c];
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < SW_R; r++) {
+                uint32_t e = base + r * SW_THREADS + tid;
+                if (e < nel) {
+                    uint32_t P = row_lo + (e >> lw);
+                    buf[(P << lw) | (e & cmask)] = v[r];
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// adjoint sweep: rows Q >= 2^(m+1) updated in decreasing order (a row only
+// reads rows <= itself).  Afterwards rows [2^nn, 2^(nn+1)) hold the result.
+template <typename T>
+__device__ void lsweep_adj(T *buf, int nn, int lw) {
+    const int tid = threadIdx.x;
+    for (int i = nn - 1; i >= 0; i--) {
+        const int m = nn - i - 1;
+        const uint32_t row_lo = 2u << m;
+        const uint32_t top = (2u << nn) - 1u;
+        const uint32_t nel = ((2u << nn) - row_lo) << lw;
+        const uint32_t cmask = (1u << lw) - 1u;
+        const uint32_t lomask = (1u << m) - 1u;
+        for (uint32_t base = 0; base < nel; base += SW_THREADS * SW_R) {
+            T v[SW_R];
+#pragma unroll
+            for (int r = 0; r < SW_R; r++) {
+                uint32_t e = base + r * SW_THREADS + tid;
+                if (e < nel) {
+                    uint32_t Q = top - (e >> lw);
+                    uint32_t c = e & cmask;
+                    uint32_t cq = ((Q >> (m + 1)) << m) | (Q & lomask);
+                    v[r] = buf[(Q << lw) | c] + buf[(cq << lw) | c];
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < SW_R; r++) {
+                uint32_t e = base + r * SW_THREADS + tid;
+                if (e < nel) {
+                    uint32_t Q = top - (e >> lw);
+                    buf[(Q << lw) | (e & cmask)] = v[r];
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ double block_sum(double v, double *red) {
+    const unsigned FULL = 0xffffffffu;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < SW_THREADS / 32; w++) s += red[w];
+    return s;
+}
+
+__device__ __forceinline__ double block_max(double v, double *red) {
+    const unsigned FULL = 0xffffffffu;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(FULL, v, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = -INFINITY;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < SW_THREADS / 32; w++) s = fmax(s, red[w]);
+    return s;
+}
+
+struct SweepArgs {
+    int n, n1, n2, lw;
+    int nblk;                 // column CTAs per instance
+    size_t strideN, strideM;  // 2^n, 2^(n+1)
+    const double *inst;
+    double *part;             // [nd][2][nblk][4]
+    int maxblk;
+    double q_floor;
+    const double *inv_binom;  // [n+1]
+};
+
+// ---------------------------------------------------------------------------
+// pass 1 forward (columns): tile = all x1 x (1<<lw) consecutive x2.
+// Prologue applies the pending BA update p <- p 2^{Dbar - shift} and writes
+// p back.  With n2 == 0 the pass covers all n symbols and writes q, L.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(SW_THREADS) k_cols_fwd(SweepArgs a, T *p, const T *D, T *F1, T *q, T *L,
+                                                          int apply_update, int mode) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *buf = reinterpret_cast<T *>(smem_raw);
+    __shared__ double red[SW_THREADS / 32];
+    const int z = blockIdx.y;
+    const double *inst = a.inst + z * INST_STRIDE;
+    if (inst[I_ACTIVE] == 0.0) return;
+    const int n1 = a.n1, n2 = a.n2, lw = a.lw;
+    const uint32_t w = 1u << lw;
+    const uint32_t col0 = blockIdx.x << lw;
+    T *pz = p + z * a.strideN;
+    const T *Dz = D + z * a.strideN;
+    const bool upd = apply_update && inst[I_PENDING] != 0.0;
+    const T shift = (T)inst[I_SHIFT];
+    const uint32_t ntop = (1u << n1) << lw;
+    double psum = 0.0;
+    for (uint32_t e = threadIdx.x; e < ntop; e += SW_THREADS) {
+        uint32_t x1 = e >> lw, c = e & (w - 1u);
+        size_t x = ((size_t)x1 << n2) | (col0 + c);
+        T v = pz[x];
+        if (upd) {
+            v = v * exp2_t<T>(Dz[x] - shift);
+            pz[x] = v;
+        }
+        buf[ntop + e] = v;
+        buf[e] = (T)0;
+        psum += (double)v;
+    }
+    double s = block_sum<T>(psum, red);
+    if (threadIdx.x == 0 && (mode == MODE_ITER || mode == MODE_DIV)) {
+        double *pp = a.part + ((size_t)z * 2 + 0) * a.maxblk * 4 + blockIdx.x * 4;
+        pp[0] = s;
+    }
+    __syncthreads();
+    lsweep_fwd<T>(buf, n1, lw);
+    if (n2 > 0) {
+        T *Fz = F1 + z * a.strideN;
+        for (uint32_t e = threadIdx.x + w; e < ntop; e += SW_THREADS) {
+            uint32_t row = e >> lw, c = e & (w - 1u);
+            Fz[((size_t)row << n2) | (col0 + c)] = buf[e];
+        }
+    } else {
+        T *qz = q + z * a.strideM, *Lz = L + z * a.strideM;
+        for (uint32_t c = threadIdx.x + 1; c < (2u << n1); c += SW_THREADS) {
+            int k = bitlen32(c) - 1;
+            T qv = buf[c] * (T)a.inv_binom[k];
+            qz[c] = qv;
+            Lz[c] = log2_t<T>(mode == MODE_CERT ? fmin(qv, (T)1) : fmax(qv, (T)a.q_floor));
+        }
+    }
+}
+
+// pass 2 forward (rows): one row c1 per CTA; input row = F1[c1] (c1 < 2^n1)
+// or p[x1 = c1 - 2^n1]; output codes c2 < 32 go to the transposed Ts.
+template <typename T>
+__global__ void __launch_bounds__(SW_THREADS) k_rows_fwd(SweepArgs a, const T *p, const T *F1, T *Tm, T *Ts) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *buf = reinterpret_cast<T *>(smem_raw);
+    const int z = blockIdx.y;
+    if (a.inst[z * INST_STRIDE + I_ACTIVE] == 0.0) return;
+    const int n1 = a.n1, n2 = a.n2;
+    const uint32_t c1 = blockIdx.x + 1;
+    const uint32_t half = 1u << n2;
+    const T *src = (c1 >= (1u << n1)) ? p + z * a.strideN + ((size_t)(c1 - (1u << n1)) << n2)
+                                      : F1 + z * a.strideN + ((size_t)c1 << n2);
+    for (uint32_t e = threadIdx.x; e < half; e += SW_THREADS) {
+        buf[half + e] = src[e];
+        buf[e] = (T)0;
+    }
+    __syncthreads();
+    lsweep_fwd<T>(buf, n2, 0);
+    T *Tmz = Tm + z * a.strideM;
+    T *Tsz = Ts + z * ((size_t)32 << (n1 + 1));
+    for (uint32_t c2 = threadIdx.x + 1; c2 < half; c2 += SW_THREADS) {
+        if (c2 < 32) Tsz[((size_t)c2 << (n1 + 1)) + c1] = buf[c2];
+        else Tmz[((size_t)c1 << n2) + c2] = buf[c2];
+    }
+}
+
+// combine: F_n(y) = sum over splits of the two passes' outputs; q_k = F_n / C(n,k)
+template <typename T>
+__global__ void k_combine(SweepArgs a, const T *p, const T *F1, const T *Tm, const T *Ts, T *q, T *L, int mode) {
+    const int z = blockIdx.y;
+    if (a.inst[z * INST_STRIDE + I_ACTIVE] == 0.0) return;
+    const int n1 = a.n1, n2 = a.n2, n = a.n;
+    const T *pz = p + z * a.strideN, *Fz = F1 + z * a.strideN, *Tmz = Tm + z * a.strideM;
+    const T *Tsz = Ts + z * ((size_t)32 << (n1 + 1));
+    T *qz = q + z * a.strideM, *Lz = L + z * a.strideM;
+    const uint32_t total = 2u << n;
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < total; c += gridDim.x * blockDim.x) {
+        if (c == 0) continue;
+        const int k = bitlen32(c) - 1;
+        const uint32_t y = c ^ (1u << k);
+        const int jlo = max(0, k - n2), jhi = min(k, n1);
+        T acc = (T)0;
+        for (int j = jlo; j <= jhi; j++) {
+            const int l = k - j;
+            const uint32_t c1 = (1u << j) | (y >> l);
+            const uint32_t u2 = y & ((1u << l) - 1u);
+            const uint32_t c2 = (1u << l) | u2;
+            T v;
+            if (l == n2) v = (c1 >= (1u << n1)) ? pz[((size_t)(c1 - (1u << n1)) << n2) | u2] : Fz[((size_t)c1 << n2) | u2];
+            else if (c2 < 32) v = Tsz[((size_t)c2 << (n1 + 1)) + c1];
+            else v = Tmz[((size_t)c1 << n2) + c2];
+            acc += v;
+        }
+        T qv = acc * (T)a.inv_binom[k];
+        qz[c] = qv;
+        Lz[c] = log2_t<T>(mode == MODE_CERT ? fmin(qv, (T)1) : fmax(qv, (T)a.q_floor));
+    }
+}
+
+// pass 2 adjoint (rows): gather omega_k L(code c1 . c2) over the row, adjoint
+// sweep over x2, write the row's top half to Gb[c1][x2].
+template <typename T>
+__global__ void __launch_bounds__(SW_THREADS) k_rows_adj(SweepArgs a, const T *Lsrc, const T *omega, T *Gb) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *buf = reinterpret_cast<T *>(smem_raw);
+    const int z = blockIdx.y;
+    if (a.inst[z * INST_STRIDE + I_ACTIVE] == 0.0) return;
+    const int n1 = a.n1, n2 = a.n2, n = a.n;
+    const uint32_t c1 = blockIdx.x + 1;
+    const int j = bitlen32(c1) - 1;
+    const T *Lz = Lsrc + z * a.strideM;
+    const T *om = omega + z * (n + 1);
+    for (uint32_t c2 = threadIdx.x; c2 < (2u << n2); c2 += SW_THREADS) {
+        T v = (T)0;
+        if (c2 > 0) {
+            int l = bitlen32(c2) - 1;
+            uint32_t code = (c1 << l) | (c2 ^ (1u << l));
+            v = om[j + l] * Lz[code];
+        }
+        buf[c2] = v;
+    }
+    __syncthreads();
+    lsweep_adj<T>(buf, n2, 0);
+    T *Gz = Gb + z * a.strideM + ((size_t)c1 << n2);
+    const uint32_t half = 1u << n2;
+    for (uint32_t e = threadIdx.x; e < half; e += SW_THREADS) Gz[e] = buf[half + e];
+    (void)n1;
+}
+
+struct EpiArgs {
+    const double *hb2;   // [nd][2^n] sum_k rho_k b_k H_k (dual-bound d-gradient)
+    const void *Hb;      // [nd][2^n] (T)
+    const void *p;       // [nd][2^n] (T)
+    void *Dout;          // [nd][2^n] T (MODE_ITER) or double (MODE_DIV / MODE_CERT spare)
+    double eH_scale;     // certify: gamma factor on |G|
+    double u;            // unit roundoff
+};
+
+// pass 1 adjoint (columns): load Gb (or omega L directly when n2 == 0), adjoint
+// sweep over x1, then the epilogue D_x = -Hb(x) - G(x) and block partials.
+template <typename T>
+__global__ void __launch_bounds__(SW_THREADS) k_cols_adj(SweepArgs a, EpiArgs ep, const T *Gb, const T *Lsrc,
+                                                          const T *omega, int mode) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *buf = reinterpret_cast<T *>(smem_raw);
+    __shared__ double red[SW_THREADS / 32];
+    const int z = blockIdx.y;
+    const double *inst = a.inst + z * INST_STRIDE;
+    if (inst[I_ACTIVE] == 0.0) return;
+    const int n1 = a.n1, n2 = a.n2, lw = a.lw, n = a.n;
+    const uint32_t w = 1u << lw;
+    const uint32_t col0 = blockIdx.x << lw;
+    const uint32_t nall = (2u << n1) << lw;
+    if (n2 > 0) {
+        const T *Gz = Gb + z * a.strideM;
+        for (uint32_t e = threadIdx.x; e < nall; e += SW_THREADS) {
+            uint32_t row = e >> lw, c = e & (w - 1u);
+            buf[e] = row ? Gz[((size_t)row << n2) | (col0 + c)] : (T)0;
+        }
+    } else {
+        const T *Lz = Lsrc + z * a.strideM;
+        const T *om = omega + z * (n + 1);
+        for (uint32_t c = threadIdx.x; c < (2u << n1); c += SW_THREADS)
+            buf[c] = c ? om[bitlen32(c) - 1] * Lz[c] : (T)0;
+    }
+    __syncthreads();
+    lsweep_adj<T>(buf, n1, lw);
+    const T *Hbz = reinterpret_cast<const T *>(ep.Hb) + z * a.strideN;
+    const T *pz = reinterpret_cast<const T *>(ep.p) + z * a.strideN;
+    const uint32_t ntop = (1u << n1) << lw;
+    double sZ = 0.0, mD = -INFINITY, sP = 0.0, mP = -INFINITY;
+    const double add = (mode == MODE_DIV) ? inst[I_SUMP] : 0.0;
+    for (uint32_t e = threadIdx.x; e < ntop; e += SW_THREADS) {
+        uint32_t x1 = e >> lw, c = e & (w - 1u);
+        size_t x = ((size_t)x1 << n2) | (col0 + c);
+        T G = buf[ntop + e];
+        T hb = Hbz[x];
+        if (mode == MODE_ITER) {
+            T Dv = -hb - G;
+            reinterpret_cast<T *>(ep.Dout)[z * a.strideN + x] = Dv;
+            double pv = (double)pz[x];
+            sZ += pv * (double)exp2_t<T>(Dv);
+            mD = fmax(mD, (double)Dv);
+        } else if (mode == MODE_DIV) {
+            double Dv = (double)(-hb - G) + add;
+            reinterpret_cast<double *>(ep.Dout)[z * a.strideN + x] = Dv;
+            mD = fmax(mD, Dv);
+        } else if (mode == MODE_DUAL) {
+            // q is a full (normalised) output marginal: D = -h(b) - Hb - G
+            double Dv = (double)(-hb - G) + inst[I_NEGH];
+            reinterpret_cast<double *>(ep.Dout)[z * a.strideN + x] = Dv;
+            mD = fmax(mD, Dv);
+        } else if (mode == MODE_DUAL_D) {
+            double Dv = reinterpret_cast<const double *>(ep.Dout)[z * a.strideN + x];
+            double pi = exp2((Dv - inst[I_DUAL_MAXD]) / inst[I_DUAL_TAU]) / inst[I_DUAL_S];
+            sZ += pi * (-ep.hb2[z * a.strideN + x] - (double)G);
+        } else {  // MODE_CERT (T = double)
+            double Gd = (double)G, Hd = (double)hb;
+            double Dv = -Hd - Gd;
+            double m = __dadd_ru(__dmul_ru(ep.eH_scale, fabs(Gd)),
+                                 __dadd_ru(__dmul_ru(1.01 * ep.u, fabs(Hd) + fabs(Gd)), inst[I_EH]));
+            double up = __dadd_ru(Dv, m);
+            reinterpret_cast<double *>(ep.Dout)[z * a.strideN + x] = Dv;
+            double pv = (double)pz[x];
+            sZ += pv * exp2(Dv);
+            sP += pv;
+            mD = fmax(mD, up);
+            mP = fmax(mP, Dv);
+        }
+    }
+    double s1 = block_sum<T>(sZ, red);
+    double s3 = block_sum<T>(sP, red);
+    double s2 = block_max(mD, red);
+    double s4 = block_max(mP, red);
+    if (threadIdx.x == 0) {
+        double *pp = a.part + ((size_t)z * 2 + 1) * a.maxblk * 4 + blockIdx.x * 4;
+        pp[0] = s1;
+        pp[1] = s2;
+        pp[2] = s3;
+        pp[3] = s4;
+    }
+}
+
+template <typename T>
+SweepArgs make_args(bdc_engine *e, PrecBuf<T> &b) {
+    SweepArgs a{};
+    a.n = e->n;
+    a.n1 = b.s.n1;
+    a.n2 = b.s.n2;
+    a.lw = b.s.lw;
+    a.nblk = b.s.nblk_cols;
+    a.strideN = (size_t)1 << e->n;
+    a.strideM = (size_t)2 << e->n;
+    a.inst = e->inst;
+    a.part = b.part;
+    a.maxblk = part_maxblk(e);
+    a.q_floor = e->opt.q_floor;
+    a.inv_binom = e->bk + (size_t)4 * e->nd * (e->n + 1);
+    return a;
+}
+
+template <typename T>
+size_t tile_bytes_cols(const Sched &s) { return ((size_t)2 << s.n1 << s.lw) * sizeof(T); }
+template <typename T>
+size_t tile_bytes_rows(const Sched &s) { return ((size_t)2 << s.n2) * sizeof(T); }
+
+template <typename K>
+cudaError_t allow_smem(K kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+Sched make_sched(int n, int elem_bytes, int n2_override, int w_override) {
+    Sched s{};
+    const int tile = (elem_bytes == 4) ? 32768 : 16384;  // elements per CTA tile (128 KB)
+    int nsingle = 0;
+    while ((2 << (nsingle + 1)) <= tile) nsingle++;       // 2^(n+1) <= tile
+    if (n <= nsingle && n2_override == 0) {
+        s.n1 = n;
+        s.n2 = 0;
+        s.lw = 0;
+        s.nblk_cols = 1;
+        return s;
+    }
+    int n2max = nsingle;
+    int n2 = n2_override ? n2_override : std::min(n - 1, n2max);
+    if (n2 < 5) n2 = std::min(5, n - 1);
+    s.n2 = n2;
+    s.n1 = n - n2;
+    int lw = 0;
+    while (lw < 5 && lw < n2 && ((size_t)2 << s.n1 << (lw + 1)) <= (size_t)tile) lw++;
+    if (w_override) {
+        lw = 0;
+        while ((1 << (lw + 1)) <= w_override) lw++;
+    }
+    s.lw = lw;
+    s.nblk_cols = 1 << (n2 - lw);
+    return s;
+}
+
+template <typename T>
+bdc_status sweep_prepare(bdc_engine *e, PrecBuf<T> &b) {
+    BDC_CUDA_TRY(allow_smem(k_cols_fwd<T>, tile_bytes_cols<T>(b.s)));
+    BDC_CUDA_TRY(allow_smem(k_cols_adj<T>, tile_bytes_cols<T>(b.s)));
+    if (b.s.n2 > 0) {
+        BDC_CUDA_TRY(allow_smem(k_rows_fwd<T>, tile_bytes_rows<T>(b.s)));
+        BDC_CUDA_TRY(allow_smem(k_rows_adj<T>, tile_bytes_rows<T>(b.s)));
+    }
+    (void)e;
+    return BDC_OK;
+}
+
+template <typename T>
+bdc_status sweep_forward(bdc_engine *e, PrecBuf<T> &b, const T *p_src, int apply_update, int mode) {
+    SweepArgs a = make_args(e, b);
+    const Sched &s = b.s;
+    size_t sm1 = tile_bytes_cols<T>(s);
+    T *p = const_cast<T *>(p_src);
+    dim3 g1(s.nblk_cols, e->nd);
+    k_cols_fwd<T><<<g1, SW_THREADS, sm1, e->stream>>>(a, p, b.D, b.F1, b.q, b.L, apply_update, mode); e->launches++; stage_mark(e, "cols_fwd");
+    BDC_CUDA_TRY(cudaGetLastError());
+    if (s.n2 > 0) {
+        size_t sm2 = tile_bytes_rows<T>(s);
+        dim3 g2((2u << s.n1) - 1u, e->nd);
+        k_rows_fwd<T><<<g2, SW_THREADS, sm2, e->stream>>>(a, p, b.F1, b.Tm, b.Ts); e->launches++; stage_mark(e, "rows_fwd");
+        BDC_CUDA_TRY(cudaGetLastError());
+        int nb = (int)std::min<size_t>(((size_t)2 << e->n) / 256 + 1, 148 * 16);
+        dim3 g3(nb, e->nd);
+        k_combine<T><<<g3, 256, 0, e->stream>>>(a, p, b.F1, b.Tm, b.Ts, b.q, b.L, mode); e->launches++; stage_mark(e, "combine");
+        BDC_CUDA_TRY(cudaGetLastError());
+    }
+    return BDC_OK;
+}
+
+template <typename T>
+bdc_status sweep_adjoint(bdc_engine *e, PrecBuf<T> &b, const T *Lsrc, const T *omega, T *Dout, int mode) {
+    SweepArgs a = make_args(e, b);
+    const Sched &s = b.s;
+    if (s.n2 > 0) {
+        size_t sm2 = tile_bytes_rows<T>(s);
+        dim3 g2((2u << s.n1) - 1u, e->nd);
+        k_rows_adj<T><<<g2, SW_THREADS, sm2, e->stream>>>(a, Lsrc, omega, b.Gb); e->launches++; stage_mark(e, "rows_adj");
+        BDC_CUDA_TRY(cudaGetLastError());
+    }
+    EpiArgs ep{};
+    ep.hb2 = e->pcert;
+    ep.Hb = b.Hb;
+    ep.p = (mode == MODE_CERT) ? (const void *)e->pcert : (const void *)b.p;
+    ep.Dout = Dout;
+    ep.u = 1.1102230246251565e-16;
+    {
+        // gamma_{n+8} * 1.01 + 1.01 u
+        double m = e->n + 8;
+        ep.eH_scale = 1.01 * (m * ep.u / (1.0 - m * ep.u)) + 1.01 * ep.u;
+    }
+    size_t sm1 = tile_bytes_cols<T>(s);
+    dim3 g1(s.nblk_cols, e->nd);
+    k_cols_adj<T><<<g1, SW_THREADS, sm1, e->stream>>>(a, ep, b.Gb, Lsrc, omega, mode); e->launches++; stage_mark(e, "cols_adj");
+    BDC_CUDA_TRY(cudaGetLastError());
+    return BDC_OK;
+}
+
+template bdc_status sweep_prepare<float>(bdc_engine *, PrecBuf<float> &);
+template bdc_status sweep_prepare<double>(bdc_engine *, PrecBuf<double> &);
+template bdc_status sweep_forward<float>(bdc_engine *, PrecBuf<float> &, const float *, int, int);
+template bdc_status sweep_forward<double>(bdc_engine *, PrecBuf<double> &, const double *, int, int);
+template bdc_status sweep_adjoint<float>(bdc_engine *, PrecBuf<float> &, const float *, const float *, float *, int);
+template bdc_status sweep_adjoint<double>(bdc_engine *, PrecBuf<double> &, const double *, const double *, double *, int);

@@ -1,0 +1,157 @@
+"""GPU parity of full Blahut-Arimoto iterations and of the certified bound.
+
+Sweep path (FP64 and FP32) and literal enumeration path (FP64) against the
+oracle's BA (Sec. 2.3) iteration by iteration; certified upper bound against
+the oracle's exact dual value (|U - U_oracle| <= 1e-6 bits, U >= the oracle's
+lower bound, margin > 0); closed forms C_1(d) = 1 - d, C_n(0) = n, C_n(1) = 0;
+stopping rule; checkpoint resume is bit-identical.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_05867_b300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _bdc():
+    import paper_2604_05867_b300 as bdc
+    return bdc
+
+
+def _engine(n, ds, **kw):
+    bdc = _bdc()
+    return bdc.Engine(n, ds, options=bdc.default_options(**kw))
+
+
+@pytest.mark.parametrize("impl,prec,tol", [("sweep", "fp64", 1e-11), ("literal", "fp64", 1e-11),
+                                           ("sweep", "fp32", 2e-5)])
+@pytest.mark.parametrize("n,d", [(4, 0.5), (7, 0.3), (10, 0.8)])
+def test_ba_iterations_match_oracle(impl, prec, tol, n, d):
+    T = 60
+    ref = oracle.ba_bdc(n, d, T)
+    eng = _engine(n, [d])
+    lo, up, it = eng.iterate(T, -1.0, prec, impl)
+    assert it[0] == T
+    hlo, hup = eng.history(0)
+    assert len(hlo) == T
+    assert np.all(np.abs(hlo - ref["lower"]) <= tol * np.maximum(1.0, np.abs(ref["lower"])))
+    assert np.all(np.abs(hup - ref["upper"]) <= tol * np.maximum(1.0, np.abs(ref["upper"])))
+    p = eng.get_p()[0]
+    ptol = 1e-9 if prec == "fp64" else 2e-3
+    assert np.all(np.abs(p - ref["p"]) <= ptol * ref["p"] + 1e-300)
+    eng.close()
+
+
+@pytest.mark.parametrize("d", [0.1, 0.5, 0.9])
+def test_bec_closed_form(d):
+    eng = _engine(1, [d])
+    lo, up, _ = eng.iterate(20, -1.0, "fp64", "sweep")
+    assert abs(lo[0] - (1 - d)) < 1e-13 and abs(up[0] - (1 - d)) < 1e-13
+    c = eng.certify()
+    assert c["upper"][0] >= 1 - d and c["upper"][0] - (1 - d) < 1e-9
+    eng.close()
+
+
+def test_noiseless_and_erased_channels():
+    n = 9
+    eng = _engine(n, [0.0, 1.0])
+    lo, up, _ = eng.iterate(2, -1.0, "fp64", "sweep")
+    assert abs(lo[0] - n) < 1e-12 and abs(up[0] - n) < 1e-12
+    assert abs(lo[1]) < 1e-12 and abs(up[1]) < 1e-12
+    eng.close()
+
+
+def test_stopping_rule_and_monotone_lower():
+    n, d, tol = 8, 0.5, 1e-3
+    ref = oracle.ba_bdc(n, d, 5000, tol=tol)
+    eng = _engine(n, [d], chunk=4)
+    lo, up, it = eng.iterate(5000, tol, "fp64", "sweep")
+    assert it[0] == ref["iters"]
+    hlo, hup = eng.history(0)
+    assert np.all(np.diff(hlo) >= -1e-12)
+    assert hup[-1] - hlo[-1] < tol
+    eng.close()
+
+
+@pytest.mark.parametrize("n,d", [(6, 0.5), (10, 0.5), (12, 0.7)])
+def test_certified_bound(n, d):
+    T = 150
+    eng = _engine(n, [d])
+    eng.iterate(T, -1.0, "fp32", "sweep")
+    c = eng.certify()
+    # oracle: exact dual value of the same certified input p~ = (1-eps)p + eps u
+    p = eng.get_p()[0]
+    eps = 2.0 ** -30
+    pt = (1 - eps) * p + eps / (1 << n)
+    q = oracle.q_full(n, d, pt)
+    U_ref, _ = oracle.certify(n, d, q)
+    lower_ref = oracle.ba_bdc(n, d, T)["lower"][-1]
+    assert c["upper"][0] >= U_ref - 1e-12
+    assert c["upper"][0] - U_ref <= 1e-6
+    assert c["upper"][0] >= lower_ref
+    assert 0 < c["margin"][0] < 1e-6
+    assert abs(c["lower"][0] - lower_ref) < 1e-3
+    eng.close()
+
+
+def test_certify_given_q():
+    n, d = 8, 0.6
+    rng = np.random.default_rng(0)
+    qh = rng.uniform(0.1, 1.0, size=2 << n)
+    qh[0] = 0.0
+    qh /= qh.sum()
+    eng = _engine(n, [d])
+    c = eng.certify(torch.tensor(qh[None, :], device="cuda"))
+    U_ref, _ = oracle.certify(n, d, qh)
+    assert U_ref - 1e-12 <= c["upper"][0] <= U_ref + 1e-6
+    assert np.isnan(c["lower"][0])
+    eng.close()
+
+
+def test_orbit_invariance_and_symmetrize():
+    n, d = 11, 0.4
+    eng = _engine(n, [d])
+    eng.iterate(40, -1.0, "fp32", "sweep")
+    p = eng.get_p()[0]
+    x = np.arange(1 << n)
+    full = (1 << n) - 1
+    rx = np.array([int(format(v, "0%db" % n)[::-1], 2) for v in x])
+    assert np.array_equal(p, p[x ^ full]) and np.array_equal(p, p[rx])
+    eng.close()
+
+
+def test_checkpoint_resume_is_bit_identical(tmp_path):
+    n, d = 9, 0.5
+    a = _engine(n, [d])
+    a.iterate(20, -1.0, "fp64", "sweep")
+    path = str(tmp_path / "ck.bin")
+    a.save(path)
+    a.iterate(15, -1.0, "fp64", "sweep")
+    pa = a.get_p()
+    b = _engine(n, [d])
+    b.load(path)
+    b.iterate(15, -1.0, "fp64", "sweep")
+    pb = b.get_p()
+    assert np.array_equal(pa, pb)
+    a.close()
+    b.close()
+
+
+def test_precision_switch_and_literal_agree():
+    n, d = 10, 0.5
+    ref = oracle.ba_bdc(n, d, 30)
+    eng = _engine(n, [d])
+    eng.iterate(10, -1.0, "fp64", "sweep")
+    eng.iterate(10, -1.0, "fp64", "literal")
+    eng.iterate(10, -1.0, "fp64", "sweep")
+    hlo, hup = eng.history(0)
+    assert np.all(np.abs(hlo - ref["lower"]) <= 1e-11)
+    assert np.all(np.abs(hup - ref["upper"]) <= 1e-11)
+    eng.close()
