@@ -173,6 +173,12 @@ bdc_status bdc_output_classes(bdc_engine *eng, int64_t *cls_host);
 bdc_status bdc_dual_bound(bdc_engine *eng, int inst, const void *theta_dev, double tau, int precision,
                           double *F, double *max_D, void *grad_theta_dev, double *grad_d);
 
+/* q = softmax of theta over output classes, written for every code into the
+ * caller's device array q_dev (doubles [2^(n+1)], slot 0 = 0), e.g. to
+ * certify an optimised q with bdc_certify_upper (one instance: pass a
+ * q_dev of nd rows when nd > 1).  theta_dev as in bdc_dual_bound. */
+bdc_status bdc_softmax_classes(bdc_engine *eng, int inst, const void *theta_dev, int precision, double *q_dev);
+
 /* --- measurement --------------------------------------------------------- */
 
 /* Number of kernels this engine has launched so far (kernels replayed inside

@@ -78,6 +78,7 @@ def lib():
             "bdc_dual_bound": (I, [P, I, P, D, I, P, P, P, P]),
             "bdc_subseq_counts": (I, [I, P, I64, P, P, P, P]),
             "bdc_launch_count": (I64, [P]),
+            "bdc_softmax_classes": (I, [P, I, P, I, P]),
             "bdc_profile_iteration": (I, [P, I, I, I, P, ctypes.c_char_p, I, P]),
             "bdc_last_error": (ctypes.c_char_p, []),
         }
@@ -266,6 +267,15 @@ class Engine:
                                     ctypes.c_void_p(g.data_ptr()) if grad else None,
                                     ctypes.byref(gd) if grad else None))
         return F.value, mD.value, g, (gd.value if grad else None)
+
+
+    def softmax_classes(self, inst: int, theta, precision="fp64"):
+        """q over every code (float64 CUDA tensor [2^(n+1)]) = softmax of theta over classes."""
+        import torch
+        q = torch.empty(2 << self.n, dtype=torch.float64, device=self.device)
+        _check(lib().bdc_softmax_classes(self._h, int(inst), ctypes.c_void_p(theta.data_ptr()), _PREC[precision],
+                                         ctypes.c_void_p(q.data_ptr())))
+        return q
 
 
 def subseq_counts(n: int, xs, emb: bool = False, stream=None):

@@ -199,7 +199,48 @@ bdc_status dual_impl(bdc_engine *e, PrecBuf<T> &b, int z, const T *theta, double
     return BDC_OK;
 }
 
+template <typename T>
+__global__ void k_make_q(size_t M, const T *theta, const int32_t *cls, const double *inst_z, double *q) {
+    const double lse = inst_z[I_DUAL_ZT];
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < M; c += (size_t)gridDim.x * blockDim.x)
+        q[c] = (c == 0) ? 0.0 : exp((double)theta[cls[c]] - lse);
+}
+
+template <typename T>
+bdc_status softmax_impl(bdc_engine *e, PrecBuf<T> &b, int z, const T *theta, double *q_out) {
+    const size_t M = (size_t)2 << e->n;
+    const int maxblk = part_maxblk(e);
+    double *iz = e->inst + (size_t)z * INST_STRIDE;
+    double *part0 = b.part + ((size_t)z * 2 + 0) * maxblk * 4;
+    const int gM = gridc(M);
+    k_theta_max<T><<<gM, RT, 0, e->stream>>>(M, theta, e->ocls, part0, 0); e->launches++;
+    k_fin<<<1, 32, 0, e->stream>>>(part0, 4, gM, 0, iz, I_DUAL_ZT, 0); e->launches++;
+    k_theta_sumexp<T><<<gM, RT, 0, e->stream>>>(M, theta, e->ocls, iz, part0); e->launches++;
+    k_fin<<<1, 32, 0, e->stream>>>(part0, 4, gM, 1, iz, I_DUAL_ZT, 1); e->launches++;
+    k_make_q<T><<<gM, RT, 0, e->stream>>>(M, theta, e->ocls, iz, q_out); e->launches++;
+    BDC_CUDA_TRY(cudaGetLastError());
+    cudaError_t err = cudaStreamSynchronize(e->stream);
+    if (err != cudaSuccess) {
+        bdc_set_error(std::string("bdc_softmax_classes: ") + cudaGetErrorString(err));
+        return BDC_ECUDA;
+    }
+    return BDC_OK;
+}
+
 }  // namespace
+
+extern "C" bdc_status bdc_softmax_classes(bdc_engine *e, int inst, const void *theta_dev, int prec, double *q_dev) {
+    if (!e || !e->bound) {
+        bdc_set_error("bdc_softmax_classes: no workspace bound");
+        return BDC_ENOTBOUND;
+    }
+    if (inst < 0 || inst >= e->nd || !theta_dev || !q_dev || (prec != BDC_FP32 && prec != BDC_FP64)) {
+        bdc_set_error("bdc_softmax_classes: bad arguments");
+        return BDC_EINVAL;
+    }
+    if (prec == BDC_FP32) return softmax_impl<float>(e, e->f32, inst, (const float *)theta_dev, q_dev);
+    return softmax_impl<double>(e, e->f64, inst, (const double *)theta_dev, q_dev);
+}
 
 extern "C" bdc_status bdc_dual_bound(bdc_engine *e, int inst, const void *theta_dev, double tau, int prec, double *F,
                                      double *max_D, void *grad_theta_dev, double *grad_d) {

@@ -519,3 +519,4 @@ template bdc_status sweep_forward<float>(bdc_engine *, PrecBuf<float> &, const f
 template bdc_status sweep_forward<double>(bdc_engine *, PrecBuf<double> &, const double *, int, int);
 template bdc_status sweep_adjoint<float>(bdc_engine *, PrecBuf<float> &, const float *, const float *, float *, int);
 template bdc_status sweep_adjoint<double>(bdc_engine *, PrecBuf<double> &, const double *, const double *, double *, int);
+
