@@ -206,6 +206,24 @@ bdc_status bdc_profile_iteration(bdc_engine *eng, int precision, int impl, int r
 bdc_status bdc_subseq_counts(int n, const uint64_t *x_dev, int64_t nx, uint64_t *N_dev, double *S_dev,
                              uint64_t *emb_dev, void *cuda_stream);
 
+/* --- allocation-free variant ------------------------------------------------ */
+
+/* Output marginal q(y) = sum_x p(x) W(y|x) of BDC_d for one d, computed by
+ * the same forward sweep as the engine but without an engine, a workspace or
+ * any device allocation.  It exists for callers that cannot allocate device
+ * memory (inside someone else's stream capture, under a host framework that
+ * owns all allocations, or under strict memory accounting); the paper has no
+ * counterpart.  Its scratch lives in one fixed device array inside the
+ * library (about 10.5 MB, held by every GPU that loads the library until the
+ * process exits), so 1 <= n <= 18.  p_dev: device doubles [2^n]; q_dev:
+ * device doubles [2^(n+1)] by code (slot 0 written 0).  Runs on cuda_stream
+ * (NULL = legacy default stream) and returns without synchronising.  All
+ * calls on a device share the array: calls that overlap on the GPU race, so
+ * the caller orders them.  The first call on a device does a one-time
+ * set-up (looks up the array's address, sets shared-memory limits) and must
+ * come before any stream capture.  n > 18 or bad arguments: BDC_EINVAL. */
+bdc_status bdc_output_marginal_static(int n, double d, const double *p_dev, double *q_dev, void *cuda_stream);
+
 /* Thread-local message of the last failing call on this thread. */
 const char *bdc_last_error(void);
 

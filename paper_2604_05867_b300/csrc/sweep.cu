@@ -520,3 +520,118 @@ template bdc_status sweep_forward<double>(bdc_engine *, PrecBuf<double> &, const
 template bdc_status sweep_adjoint<float>(bdc_engine *, PrecBuf<float> &, const float *, const float *, float *, int);
 template bdc_status sweep_adjoint<double>(bdc_engine *, PrecBuf<double> &, const double *, const double *, double *, int);
 
+// ---------------------------------------------------------------------------
+// Output marginal without any device allocation.
+//
+// Some callers cannot allocate device memory at all: code that runs inside a
+// CUDA graph being captured by someone else, plugins whose host framework
+// owns every allocation and forbids cudaMalloc, or memory-accounted jobs
+// that must not grow the device heap.  For them, the forward sweep below
+// keeps all of its scratch (the column-pass output, the row-pass output, the
+// log table and a few scalars) in one file-scope device array of fixed size,
+// reserved when the library is loaded and held by every GPU that loads it
+// until the process exits.  The caller passes only the input distribution
+// and the output buffer.
+//
+// Limits and sharing: n <= BDC_STATIC_MAXN (the array is sized for it); all
+// calls on a device share the one array and it keeps the last call's values,
+// so calls that overlap on the GPU (different streams, or the same stream
+// from two host threads without ordering) race and must be serialised by the
+// caller.  The first call on a device looks up the array's device address
+// (cudaGetSymbolAddress, with that device current) and sets the kernels'
+// shared-memory limits; make that first call before any stream capture.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int STATIC_MAXN = 18;
+// scalars and weights (256) + F1 (2^n) + Tm (2^(n+1)) + Ts (32 * 2^(n1+1), n1 <= 5 with the FP64
+// schedule for n <= 18) + L (2^(n+1)): 1,313,024 doubles = 10.5 MB
+constexpr size_t STATIC_DOUBLES = 256 + ((size_t)5 << STATIC_MAXN) + (size_t)32 * 64;
+
+static __device__ __align__(256) double g_static_scratch[STATIC_DOUBLES];
+
+__global__ void k_static_init(int n, double d, double *inst, double *wk, double *q_out) {
+    int t = threadIdx.x;
+    if (t < INST_STRIDE) inst[t] = (t == I_ACTIVE) ? 1.0 : 0.0;
+    if (t <= n) wk[t] = pow(d, (double)(n - t)) * pow(1.0 - d, (double)t);  // d^(n-k) (1-d)^k
+    if (t == 0) q_out[0] = 0.0;
+}
+
+struct StaticDev {
+    double *base = nullptr;
+};
+StaticDev g_static_dev[64];
+
+}  // namespace
+
+extern "C" bdc_status bdc_output_marginal_static(int n, double d, const double *p_dev, double *q_dev,
+                                                 void *cuda_stream) {
+    if (n < 1 || n > STATIC_MAXN) {
+        bdc_set_error("bdc_output_marginal_static: n must be in [1, 18]; the fixed scratch array holds no more");
+        return BDC_EINVAL;
+    }
+    if (!(d >= 0.0 && d <= 1.0) || !p_dev || !q_dev) {
+        bdc_set_error("bdc_output_marginal_static: need 0 <= d <= 1 and non-NULL p, q");
+        return BDC_EINVAL;
+    }
+    int dev = 0;
+    BDC_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) {
+        bdc_set_error("bdc_output_marginal_static: device index above 63");
+        return BDC_EINVAL;
+    }
+    const Sched s = make_sched(n, 8, 0, 0);
+    if (!g_static_dev[dev].base) {
+        // once per device, with that device current
+        void *ptr = nullptr;
+        cudaError_t err = cudaGetSymbolAddress(&ptr, g_static_scratch);
+        if (err != cudaSuccess || !ptr) {
+            bdc_set_error(std::string("bdc_output_marginal_static: cudaGetSymbolAddress: ") + cudaGetErrorString(err));
+            return BDC_ECUDA;
+        }
+        const Sched smax = make_sched(STATIC_MAXN, 8, 0, 0);
+        size_t cols = std::max(tile_bytes_cols<double>(smax), tile_bytes_cols<double>(make_sched(13, 8, 0, 0)));
+        BDC_CUDA_TRY(allow_smem(k_cols_fwd<double>, std::max(cols, tile_bytes_cols<double>(s))));
+        BDC_CUDA_TRY(allow_smem(k_rows_fwd<double>, tile_bytes_rows<double>(smax)));
+        g_static_dev[dev].base = (double *)ptr;
+    }
+    double *base = g_static_dev[dev].base;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const size_t N = (size_t)1 << n;
+    double *inst = base;                       // INST_STRIDE doubles
+    double *wk = base + 64;                    // n+1 doubles
+    double *F1 = base + 256;                   // 2^n
+    double *Tm = F1 + N;                       // 2^(n+1)
+    double *Ts = Tm + 2 * N;                   // 32 * 2^(n1+1)
+    double *L = Ts + (size_t)32 * ((size_t)2 << s.n1);  // 2^(n+1)
+    double *part = base;                       // block partials: not written in this mode
+    if ((size_t)(L + 2 * N - base) > STATIC_DOUBLES) {
+        bdc_set_error("bdc_output_marginal_static: schedule does not fit the fixed scratch array");
+        return BDC_EINVAL;
+    }
+    SweepArgs a{};
+    a.n = n;
+    a.n1 = s.n1;
+    a.n2 = s.n2;
+    a.lw = s.lw;
+    a.nblk = s.nblk_cols;
+    a.strideN = N;
+    a.strideM = 2 * N;
+    a.inst = inst;
+    a.part = part;
+    a.maxblk = 0;
+    a.q_floor = 1e-300;
+    a.inv_binom = wk;  // the combine's per-length weight: d^(n-k)(1-d)^k gives q(y) = sum_x p W
+    k_static_init<<<1, 64, 0, st>>>(n, d, inst, wk, q_dev);
+    double *p = const_cast<double *>(p_dev);  // read only: no update is applied
+    k_cols_fwd<double><<<dim3(s.nblk_cols, 1), SW_THREADS, tile_bytes_cols<double>(s), st>>>(
+        a, p, p, F1, q_dev, L, 0, MODE_DUAL);
+    if (s.n2 > 0) {
+        k_rows_fwd<double><<<dim3((2u << s.n1) - 1u, 1), SW_THREADS, tile_bytes_rows<double>(s), st>>>(a, p, F1, Tm,
+                                                                                                     Ts);
+        int nb = (int)std::min<size_t>((2 * N) / 256 + 1, 148 * 16);
+        k_combine<double><<<dim3(nb, 1), 256, 0, st>>>(a, p, F1, Tm, Ts, q_dev, L, MODE_DUAL);
+    }
+    BDC_CUDA_TRY(cudaGetLastError());
+    return BDC_OK;
+}
