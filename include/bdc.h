@@ -114,6 +114,21 @@ void bdc_destroy(bdc_engine *eng);
 bdc_status bdc_ba_iterate(bdc_engine *eng, int max_iters, double gap_tol_bits, int precision, int impl,
                           double *lower, double *upper, int *iters_done);
 
+/* A batch iterates several bound engines (different n, each with its own d
+ * values) from one CUDA graph: every engine's iterations are captured on a
+ * stream forked from their common stream, so small instances run
+ * concurrently.  Engines must share one non-default stream and must not be
+ * used elsewhere while the batch iterates.  Iterations run in multiples of
+ * `chunk` (per launch of the graph); each instance still stops on its own
+ * gap.  Results are read per engine (bdc_get_history, bdc_certify_upper). */
+typedef struct bdc_batch bdc_batch;
+bdc_status bdc_batch_create(bdc_engine *const *engines, int count, int chunk, bdc_batch **out);
+/* Sweep path only.  *iters_launched = iterations the graph ran (a multiple of
+ * chunk, at least max_iters unless every instance stopped earlier). */
+bdc_status bdc_batch_iterate(bdc_batch *batch, int max_iters, double gap_tol_bits, int precision,
+                             int *iters_launched);
+void bdc_batch_destroy(bdc_batch *batch);
+
 /* Copy the per-iteration bound history of instance inst (the last
  * min(len, 8192) iterations since bdc_bind or bdc_set_p) into host arrays;
  * returns the number of entries written in *count. */
@@ -193,6 +208,18 @@ int64_t bdc_launch_count(const bdc_engine *eng);
  * they advance p like bdc_ba_iterate. */
 bdc_status bdc_profile_iteration(bdc_engine *eng, int precision, int impl, int reps, double *stage_ms, char *names,
                                  int names_len, int *nstages);
+
+/* Schedule of the sweep in `precision`: input split n1 + n2 (n2 = 0: one
+ * pass) and the column tile width. */
+bdc_status bdc_get_schedule(const bdc_engine *eng, int precision, int *n1, int *n2, int *width);
+
+/* Autotune the sweep schedule of `precision` on this engine: time `reps`
+ * forward + adjoint sweeps of every candidate split (n2 in [max(8, n-14),
+ * 13 or 14]) and column width, keep the fastest (*best_ms = its time per
+ * forward + adjoint pair).  With n2 > 0, set that schedule instead of
+ * searching (e.g. from a cache).  The current p is kept (its pending update
+ * is applied first); cached graphs are rebuilt on the next iteration. */
+bdc_status bdc_autotune(bdc_engine *eng, int precision, int reps, int n2, int width, double *best_ms);
 
 /* --- test hook ------------------------------------------------------------ */
 

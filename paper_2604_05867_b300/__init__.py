@@ -79,6 +79,11 @@ def lib():
             "bdc_subseq_counts": (I, [I, P, I64, P, P, P, P]),
             "bdc_launch_count": (I64, [P]),
             "bdc_softmax_classes": (I, [P, I, P, I, P]),
+            "bdc_batch_create": (I, [P, I, I, P]),
+            "bdc_get_schedule": (I, [P, I, P, P, P]),
+            "bdc_autotune": (I, [P, I, I, I, I, P]),
+            "bdc_batch_iterate": (I, [P, I, D, I, P]),
+            "bdc_batch_destroy": (None, [P]),
             "bdc_profile_iteration": (I, [P, I, I, I, P, ctypes.c_char_p, I, P]),
             "bdc_last_error": (ctypes.c_char_p, []),
         }
@@ -171,6 +176,38 @@ class Engine:
         cnt = ctypes.c_int(0)
         _check(lib().bdc_get_history(self._h, inst, _np_ptr(lo), _np_ptr(up), length, ctypes.byref(cnt)))
         return lo[:cnt.value], up[:cnt.value]
+
+    def schedule(self, precision="fp32"):
+        n1, n2, w = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().bdc_get_schedule(self._h, _PREC[precision], ctypes.byref(n1), ctypes.byref(n2), ctypes.byref(w)))
+        return {"n1": n1.value, "n2": n2.value, "width": w.value}
+
+    def autotune(self, precision="fp32", reps: int = 3, cache: Optional[str] = None):
+        """Pick the fastest sweep schedule for this engine (bdc_autotune).  With
+        `cache` (a JSON file path) a result stored for this GPU model, n and
+        precision is reused, and a new result is stored."""
+        import json
+        import torch
+        key = "%s|n=%d|%s" % (torch.cuda.get_device_name(self.device), self.n, precision)
+        table = {}
+        if cache and os.path.exists(cache):
+            with open(cache) as f:
+                table = json.load(f)
+        ms = ctypes.c_double(0)
+        if key in table:
+            s = table[key]
+            _check(lib().bdc_autotune(self._h, _PREC[precision], 1, int(s["n2"]), int(s["width"]), ctypes.byref(ms)))
+            return dict(s, cached=True)
+        _check(lib().bdc_autotune(self._h, _PREC[precision], int(reps), 0, 0, ctypes.byref(ms)))
+        s = self.schedule(precision)
+        s["ms_per_sweep_pair"] = ms.value
+        if cache:
+            table[key] = s
+            tmp = cache + ".tmp%d" % os.getpid()
+            with open(tmp, "w") as f:
+                json.dump(table, f, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
+        return dict(s, cached=False)
 
     def launch_count(self) -> int:
         return int(lib().bdc_launch_count(self._h))
@@ -276,6 +313,35 @@ class Engine:
         _check(lib().bdc_softmax_classes(self._h, int(inst), ctypes.c_void_p(theta.data_ptr()), _PREC[precision],
                                          ctypes.c_void_p(q.data_ptr())))
         return q
+
+
+class Batch:
+    """Several engines iterated by one CUDA graph (bdc_batch_*).  The engines
+    must have been created on the same stream."""
+
+    def __init__(self, engines, chunk: int = 8):
+        self.engines = list(engines)
+        arr = (ctypes.c_void_p * len(self.engines))(*[e._h.value for e in self.engines])
+        h = ctypes.c_void_p()
+        _check(lib().bdc_batch_create(ctypes.cast(arr, ctypes.c_void_p), len(self.engines), int(chunk),
+                                      ctypes.byref(h)))
+        self._h = h
+
+    def iterate(self, max_iters: int, tol: float = -1.0, precision="fp32") -> int:
+        n = ctypes.c_int(0)
+        _check(lib().bdc_batch_iterate(self._h, int(max_iters), float(tol), _PREC[precision], ctypes.byref(n)))
+        return n.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().bdc_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def subseq_counts(n: int, xs, emb: bool = False, stream=None):

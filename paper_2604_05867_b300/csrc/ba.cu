@@ -43,21 +43,19 @@ __global__ void k_build_Hb(int n, int nd, const uint32_t *reps, int64_t R, const
     }
 }
 
-// one thread per instance; partials summed in block order (deterministic)
+// one block per instance; partials reduced in a fixed order (deterministic)
 __global__ void k_finalize_iter(int nd, const double *part, int maxblk, int nblk0, int nblk1, double *inst,
                                 double *hist) {
-    int z = blockIdx.x * blockDim.x + threadIdx.x;
-    if (z >= nd) return;
+    __shared__ double red[FIN_THREADS / 32];
+    const int z = blockIdx.x;
     double *I = inst + z * INST_STRIDE;
     if (I[I_ACTIVE] == 0.0) return;
     const double *p0 = part + ((size_t)z * 2 + 0) * maxblk * 4;
     const double *p1 = part + ((size_t)z * 2 + 1) * maxblk * 4;
-    double Zp = 0.0, ZD = 0.0, mD = -INFINITY;
-    for (int b = 0; b < nblk0; b++) Zp += p0[b * 4];
-    for (int b = 0; b < nblk1; b++) {
-        ZD += p1[b * 4];
-        mD = fmax(mD, p1[b * 4 + 1]);
-    }
+    double Zp = fin_sum(p0, 4, nblk0, red);
+    double ZD = fin_sum(p1, 4, nblk1, red);
+    double mD = fin_max(p1 + 1, 4, nblk1, red);
+    if (threadIdx.x != 0) return;
     if (!isfinite(ZD) || !isfinite(mD) || !(Zp > 0.0) || !isfinite(Zp) || !(ZD > 0.0)) {
         I[I_STATUS] = (double)BDC_ENONFINITE;
         I[I_ACTIVE] = 0.0;
@@ -84,12 +82,12 @@ __global__ void k_finalize_iter(int nd, const double *part, int maxblk, int nblk
 // (add_negh: q is a full output marginal, so the length entropy -h(b) does
 // not cancel and joins the constant)
 __global__ void k_finalize_sum(int nd, const double *part, int maxblk, int nblk, double *inst, int add_negh) {
-    int z = blockIdx.x * blockDim.x + threadIdx.x;
-    if (z >= nd) return;
+    __shared__ double red[FIN_THREADS / 32];
+    const int z = blockIdx.x;
     const double *p0 = part + ((size_t)z * 2 + 0) * maxblk * 4;
-    double s = 0.0;
-    for (int b = 0; b < nblk; b++) s += p0[b * 4];
-    inst[z * INST_STRIDE + I_SUMP] = log2(s) + (add_negh ? inst[z * INST_STRIDE + I_NEGH] : 0.0);
+    double s = fin_sum(p0, 4, nblk, red);
+    if (threadIdx.x == 0)
+        inst[z * INST_STRIDE + I_SUMP] = log2(s) + (add_negh ? inst[z * INST_STRIDE + I_NEGH] : 0.0);
 }
 
 // orbit mean of D (Appendix A symmetry).  x = (h | mid | l) with hb-bit h and
@@ -124,14 +122,16 @@ __global__ void k_symmetrize(int n, T *D, const double *inst) {
         tile[e] = Dz[x];
     }
     __syncthreads();
+    // every element: the mean over its orbit, summed in the order of the
+    // orbit representative's members, so all members get the same bits
     const uint32_t full = (1u << n) - 1u;
     for (uint32_t e = threadIdx.x; e < nt * TS; e += blockDim.x) {
         uint32_t t = e / TS, r = e % TS;
         uint32_t h = r >> hb, l = r & (H - 1u);
         uint32_t x = (h << (n - hb)) | (mids[t] << hb) | l;
-        if (orbit_rep_dev(x, n, nullptr) != x) continue;
-        uint32_t rx = rev_bits(x, n);
-        uint32_t mem[4] = {x, x ^ full, rx, rx ^ full};
+        uint32_t rp = orbit_rep_dev(x, n, nullptr);
+        uint32_t rr = rev_bits(rp, n);
+        uint32_t mem[4] = {rp, rp ^ full, rr, rr ^ full};
         T v[4];
         for (int s = 0; s < 4; s++) {
             uint32_t y = mem[s];
@@ -141,8 +141,7 @@ __global__ void k_symmetrize(int n, T *D, const double *inst) {
                 if (mids[q] == ym) ti = q;
             v[s] = tile[ti * TS + ((y >> (n - hb)) << hb) + (y & (H - 1u))];
         }
-        T avg = ((v[0] + v[1]) + (v[2] + v[3])) * (T)0.25;
-        for (int s = 0; s < 4; s++) Dz[mem[s]] = avg;
+        Dz[x] = ((v[0] + v[1]) + (v[2] + v[3])) * (T)0.25;
     }
 }
 
@@ -295,19 +294,19 @@ template <typename T>
 bdc_status launch_finalize(bdc_engine *e, PrecBuf<T> &b, int mode, int add_negh) {
     int maxblk = part_maxblk(e);
     if (mode == MODE_ITER) {
-        k_finalize_iter<<<(e->nd + 63) / 64, 64, 0, e->stream>>>(e->nd, b.part, maxblk, b.s.nblk_cols,
-                                                                 b.s.nblk_cols, e->inst, e->hist); e->launches++; stage_mark(e, "finalize");
+        k_finalize_iter<<<e->nd, FIN_THREADS, 0, e->stream>>>(e->nd, b.part, maxblk, b.s.nblk_cols, b.s.nblk_cols,
+                                                              e->inst, e->hist); e->launches++; stage_mark(e, "finalize");
     } else {
-        k_finalize_sum<<<(e->nd + 63) / 64, 64, 0, e->stream>>>(e->nd, b.part, maxblk, b.s.nblk_cols, e->inst,
-                                                                add_negh); e->launches++;
+        k_finalize_sum<<<e->nd, FIN_THREADS, 0, e->stream>>>(e->nd, b.part, maxblk, b.s.nblk_cols, e->inst,
+                                                             add_negh); e->launches++;
     }
     BDC_CUDA_TRY(cudaGetLastError());
     return BDC_OK;
 }
 
 bdc_status launch_finalize_literal(bdc_engine *e, int nblk0, int nblk1) {
-    k_finalize_iter<<<(e->nd + 63) / 64, 64, 0, e->stream>>>(e->nd, e->f64.part, part_maxblk(e), nblk0, nblk1,
-                                                             e->inst, e->hist); e->launches++; stage_mark(e, "finalize");
+    k_finalize_iter<<<e->nd, FIN_THREADS, 0, e->stream>>>(e->nd, e->f64.part, part_maxblk(e), nblk0, nblk1, e->inst,
+                                                          e->hist); e->launches++; stage_mark(e, "finalize");
     BDC_CUDA_TRY(cudaGetLastError());
     return BDC_OK;
 }

@@ -123,7 +123,8 @@ struct bdc_engine {
     uint32_t *counter = nullptr;  // work counters (16 words)
     uint32_t *scan_tmp = nullptr; // block counts for compaction
     double *bk = nullptr;       // [nd][n+1] b_k (FP64, host-exact)
-    double *tab_clog = nullptr; // [4096] c*log2(c)
+    double *tab_clog = nullptr; // [8192]: c*log2(c) and log2(c) for c < 4096 (literal path)
+    long long *tab_fix = nullptr; // [65536] round(c*log2(c)*2^34)
     double *inst = nullptr;     // [nd][INST_STRIDE]
     double *hist = nullptr;     // [nd][2][BDC_HIST]
     double *lit_part = nullptr; // literal path partial buffer
@@ -195,7 +196,7 @@ int64_t literal_items(int n);
 size_t literal_part_bytes(int n, int nd);
 bdc_status upload_literal_tables(bdc_engine *e);
 bdc_status subseq_counts_impl(int n, const uint64_t *x_dev, int64_t nx, uint64_t *N_dev, double *S_dev,
-                              uint64_t *emb_dev, cudaStream_t st, const double *tab_clog);
+                              uint64_t *emb_dev, cudaStream_t st, const long long *tab_fix);
 
 // record a stage boundary when profiling (no-op otherwise)
 inline void stage_mark(bdc_engine *e, const char *name) {
@@ -230,6 +231,35 @@ __device__ __forceinline__ uint32_t orbit_rep_dev(uint32_t s, int L, int *osize)
         *osize = cnt;
     }
     return m;
+}
+
+// Deterministic block reductions of block partials (blockDim.x = FIN_THREADS):
+// thread t folds elements t, t+FIN_THREADS, ... in order, then a fixed
+// shuffle tree and an in-order sum of the warp results.  Result in thread 0.
+constexpr int FIN_THREADS = 256;
+__device__ __forceinline__ double fin_sum(const double *a, int stride, int count, double *red) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < count; i += FIN_THREADS) s += a[(size_t)i * stride];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < FIN_THREADS / 32; w++) t += red[w];
+    return t;
+}
+__device__ __forceinline__ double fin_max(const double *a, int stride, int count, double *red) {
+    double s = -INFINITY;
+    for (int i = threadIdx.x; i < count; i += FIN_THREADS) s = fmax(s, a[(size_t)i * stride]);
+    for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    double t = -INFINITY;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < FIN_THREADS / 32; w++) t = fmax(t, red[w]);
+    return t;
 }
 
 template <typename T>

@@ -62,12 +62,9 @@ __global__ void k_theta_sumexp(size_t M, const T *theta, const int32_t *cls, con
 // op 1: inst[dst] = inst[dst] + log(sum part[b*4+slot])       (log-sum-exp of theta)
 // op 2: inst[dst] = sum part[b*4+slot]
 __global__ void k_fin(const double *part, int stride4, int nb, int slot, double *inst_z, int dst, int op) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double acc = (op == 0) ? -INFINITY : 0.0;
-    for (int b = 0; b < nb; b++) {
-        double v = part[b * stride4 + slot];
-        acc = (op == 0) ? fmax(acc, v) : acc + v;
-    }
+    __shared__ double red[FIN_THREADS / 32];
+    double acc = (op == 0) ? fin_max(part + slot, stride4, nb, red) : fin_sum(part + slot, stride4, nb, red);
+    if (threadIdx.x != 0) return;
     if (op == 1) inst_z[dst] = inst_z[dst] + log(acc);
     else inst_z[dst] = acc;
 }
@@ -154,17 +151,17 @@ bdc_status dual_impl(bdc_engine *e, PrecBuf<T> &b, int z, const T *theta, double
     k_activate_one<<<(nd + 63) / 64, 64, 0, e->stream>>>(nd, e->inst, z, tau); e->launches++;
     // log-sum-exp of theta over codes, then L = log2 softmax
     k_theta_max<T><<<gM, RT, 0, e->stream>>>(M, theta, e->ocls, part0, 0); e->launches++;
-    k_fin<<<1, 32, 0, e->stream>>>(part0, 4, gM, 0, iz, I_DUAL_ZT, 0); e->launches++;
+    k_fin<<<1, FIN_THREADS, 0, e->stream>>>(part0, 4, gM, 0, iz, I_DUAL_ZT, 0); e->launches++;
     k_theta_sumexp<T><<<gM, RT, 0, e->stream>>>(M, theta, e->ocls, iz, part0); e->launches++;
-    k_fin<<<1, 32, 0, e->stream>>>(part0, 4, gM, 1, iz, I_DUAL_ZT, 1); e->launches++;
+    k_fin<<<1, FIN_THREADS, 0, e->stream>>>(part0, 4, gM, 1, iz, I_DUAL_ZT, 1); e->launches++;
     k_make_L<T><<<gM, RT, 0, e->stream>>>(M, theta, e->ocls, iz, Lz); e->launches++;
     BDC_CUDA_TRY(cudaGetLastError());
     // D_x for every input (double, into the spare array), block maxima
     BDC_TRY(sweep_adjoint<T>(e, b, b.aux, b.omega, reinterpret_cast<T *>(e->marg), MODE_DUAL));
-    k_fin<<<1, 32, 0, e->stream>>>(part1, 4, b.s.nblk_cols, 1, iz, I_DUAL_MAXD, 0); e->launches++;
+    k_fin<<<1, FIN_THREADS, 0, e->stream>>>(part1, 4, b.s.nblk_cols, 1, iz, I_DUAL_MAXD, 0); e->launches++;
     const double *Dz = e->marg + z * N;
     k_pi_sum<<<gN, RT, 0, e->stream>>>(N, Dz, iz, tau, part0); e->launches++;
-    k_fin<<<1, 32, 0, e->stream>>>(part0, 4, gN, 0, iz, I_DUAL_S, 2); e->launches++;
+    k_fin<<<1, FIN_THREADS, 0, e->stream>>>(part0, 4, gN, 0, iz, I_DUAL_S, 2); e->launches++;
     k_pi_write<T><<<gN, RT, 0, e->stream>>>(N, Dz, iz, tau, b.pd + z * N); e->launches++;
     BDC_CUDA_TRY(cudaGetLastError());
     if (grad) {
@@ -179,7 +176,7 @@ bdc_status dual_impl(bdc_engine *e, PrecBuf<T> &b, int z, const T *theta, double
         // sum_x pi_x (-Hb'(x) - G'(x)), Hb' = sum_k rho_k b_k H_k, G' with weights rho_k b_k / C(n,k)
         BDC_TRY(launch_build_Hb_w(e, e->dual_w, e->pcert));
         BDC_TRY(sweep_adjoint<T>(e, b, b.aux, b.omega2, reinterpret_cast<T *>(e->marg), MODE_DUAL_D));
-        k_fin<<<1, 32, 0, e->stream>>>(part1, 4, b.s.nblk_cols, 0, iz, I_DUAL_GD, 2); e->launches++;
+        k_fin<<<1, FIN_THREADS, 0, e->stream>>>(part1, 4, b.s.nblk_cols, 0, iz, I_DUAL_GD, 2); e->launches++;
         BDC_CUDA_TRY(cudaGetLastError());
     }
     std::vector<double> h(INST_STRIDE);
@@ -214,9 +211,9 @@ bdc_status softmax_impl(bdc_engine *e, PrecBuf<T> &b, int z, const T *theta, dou
     double *part0 = b.part + ((size_t)z * 2 + 0) * maxblk * 4;
     const int gM = gridc(M);
     k_theta_max<T><<<gM, RT, 0, e->stream>>>(M, theta, e->ocls, part0, 0); e->launches++;
-    k_fin<<<1, 32, 0, e->stream>>>(part0, 4, gM, 0, iz, I_DUAL_ZT, 0); e->launches++;
+    k_fin<<<1, FIN_THREADS, 0, e->stream>>>(part0, 4, gM, 0, iz, I_DUAL_ZT, 0); e->launches++;
     k_theta_sumexp<T><<<gM, RT, 0, e->stream>>>(M, theta, e->ocls, iz, part0); e->launches++;
-    k_fin<<<1, 32, 0, e->stream>>>(part0, 4, gM, 1, iz, I_DUAL_ZT, 1); e->launches++;
+    k_fin<<<1, FIN_THREADS, 0, e->stream>>>(part0, 4, gM, 1, iz, I_DUAL_ZT, 1); e->launches++;
     k_make_q<T><<<gM, RT, 0, e->stream>>>(M, theta, e->ocls, iz, q_out); e->launches++;
     BDC_CUDA_TRY(cudaGetLastError());
     cudaError_t err = cudaStreamSynchronize(e->stream);

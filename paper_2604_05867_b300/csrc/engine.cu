@@ -115,19 +115,17 @@ __global__ void k_log2_codes_nd(const T *q, T *L, size_t per, int nd, int min1) 
 // certified upper bound: U = max_x up(D'_x + m_x) + up(log2 sum q~ + e_Lambda)
 __global__ void k_finalize_cert(int nd, const double *part, int maxblk, int nb0, int nb1, double Kterms,
                                 int have_lower, double *inst) {
-    int z = blockIdx.x * blockDim.x + threadIdx.x;
-    if (z >= nd) return;
+    __shared__ double red[FIN_THREADS / 32];
+    const int z = blockIdx.x;
     const double u = 1.1102230246251565e-16;
     const double *p0 = part + ((size_t)z * 2 + 0) * maxblk * 4;
     const double *p1 = part + ((size_t)z * 2 + 1) * maxblk * 4;
-    double sq = 0.0, S1 = 0.0, Sp = 0.0, mUp = -INFINITY, mPl = -INFINITY;
-    for (int b = 0; b < nb0; b++) sq += p0[b * 4];
-    for (int b = 0; b < nb1; b++) {
-        S1 += p1[b * 4];
-        mUp = fmax(mUp, p1[b * 4 + 1]);
-        Sp += p1[b * 4 + 2];
-        mPl = fmax(mPl, p1[b * 4 + 3]);
-    }
+    double sq = fin_sum(p0, 4, nb0, red);
+    double S1 = fin_sum(p1, 4, nb1, red);
+    double mUp = fin_max(p1 + 1, 4, nb1, red);
+    double Sp = fin_sum(p1 + 2, 4, nb1, red);
+    double mPl = fin_max(p1 + 3, 4, nb1, red);
+    if (threadIdx.x != 0) return;
     double *I = inst + z * INST_STRIDE;
     double Lam = log2(sq);
     double g = (Kterms + 3.0) * u / (1.0 - (Kterms + 3.0) * u);
@@ -180,10 +178,12 @@ void carve_prec(Carver &c, PrecBuf<T> &b, int n, int nd, int maxblk) {
     b.omega = c.take<T>((size_t)nd * (n + 1));
     b.omega2 = c.take<T>((size_t)nd * (n + 1));
     b.part = c.take<double>((size_t)nd * 2 * maxblk * 4);
-    if (b.s.n2 > 0) {
+    if (b.s.n2 > 0 || n >= 15) {
+        // sized for every split the autotuner may choose (n2 >= 8, so n1 <= n - 8)
+        int n1max = std::max(b.s.n2 > 0 ? b.s.n1 : 0, n - 8);
         b.F1 = c.take<T>(nd * N);
         b.Tm = c.take<T>(nd * M);
-        b.Ts = c.take<T>((size_t)nd * 32 * ((size_t)2 << b.s.n1));
+        b.Ts = c.take<T>((size_t)nd * 32 * ((size_t)2 << n1max));
         b.Gb = c.take<T>(nd * M);
     } else {
         b.F1 = b.Tm = b.Ts = b.Gb = nullptr;
@@ -205,6 +205,7 @@ size_t carve(bdc_engine *e, char *base) {
     e->scan_tmp = c.take<uint32_t>(M / 2048 + 16);
     e->bk = c.take<double>((size_t)6 * nd * (n + 1));
     e->tab_clog = c.take<double>(8192);
+    e->tab_fix = c.take<long long>(65536);
     e->inst = c.take<double>((size_t)nd * INST_STRIDE);
     e->hist = c.take<double>((size_t)nd * 2 * BDC_HIST);
     e->pcert = c.take<double>(nd * N);
@@ -310,8 +311,6 @@ extern "C" bdc_status bdc_bind(bdc_engine *e, void *ws, size_t bytes, void *stre
     std::vector<double> bk((size_t)6 * nd * (n + 1), 0.0);
     std::vector<double> rb((size_t)nd * (n + 1), 0.0), rw((size_t)nd * (n + 1), 0.0);
     std::vector<double> inst((size_t)nd * INST_STRIDE, 0.0);
-    uint64_t Nmax = 0;
-    for (int k = 0; k <= n; k++) Nmax = std::max<uint64_t>(Nmax, (uint64_t)std::min(std::ldexp(1.0, k), binom_d(n, k)));
     for (int z = 0; z < nd; z++) {
         long double d = e->d[z], dm = 1.0L - d;
         double sum_blc = 0.0;
@@ -340,9 +339,13 @@ extern "C" bdc_status bdc_bind(bdc_engine *e, void *ws, size_t bytes, void *stre
         double *I = &inst[(size_t)z * INST_STRIDE];
         I[I_ACTIVE] = 1.0;
         I[I_TOL] = -1.0;
-        // certified bound on |Hb^ - Hb| (summation of N_{x,k} terms, log2 and
-        // products, and the sum over k): 1.05 gamma_{Nmax+n+12} sum_k b_k log2 C(n,k)
-        I[I_EH] = 1.05 * gamma_u((double)Nmax + n + 12) * sum_blc;
+        // certified bound on |Hb^ - Hb|: S_k is an exact int64 sum of terms each
+        // within 1.125 * 2^-35 (+4u relative for counts >= 65536) of
+        // count*log2(count), converted with one rounding; with N_k <= C(n,k)
+        // and S_k/C(n,k) <= log2 C(n,k): |H^_k - H_k| <= 2^-34 + 9u log2 C(n,k),
+        // then the products and the (n+1)-term sum:
+        // 1.05 (2^-34 + gamma_{n+14} sum_k b_k log2 C(n,k))
+        I[I_EH] = 1.05 * (std::ldexp(1.0, -34) + gamma_u((double)n + 14) * sum_blc);
         I[I_NEGH] = (double)negh;
         I[I_DUAL_C0] = (double)c0;
     }
@@ -351,6 +354,8 @@ extern "C" bdc_status bdc_bind(bdc_engine *e, void *ws, size_t bytes, void *stre
         tab[c] = (double)((long double)c * log2l((long double)c));
         tab[4096 + c] = (double)log2l((long double)c);
     }
+    std::vector<long long> tabfix(65536, 0);
+    for (int c = 2; c < 65536; c++) tabfix[c] = llrintl((long double)c * log2l((long double)c) * 17179869184.0L);
     BDC_CUDA_TRY(cudaMemcpyAsync(e->bk, bk.data(), bk.size() * sizeof(double), cudaMemcpyHostToDevice, e->stream));
     BDC_CUDA_TRY(cudaMemcpyAsync(e->dual_w, rb.data(), rb.size() * sizeof(double), cudaMemcpyHostToDevice,
                                  e->stream));
@@ -358,6 +363,8 @@ extern "C" bdc_status bdc_bind(bdc_engine *e, void *ws, size_t bytes, void *stre
                                  e->stream));
     BDC_CUDA_TRY(cudaMemcpyAsync(e->tab_clog, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice,
                                  e->stream));
+    BDC_CUDA_TRY(cudaMemcpyAsync(e->tab_fix, tabfix.data(), tabfix.size() * sizeof(long long),
+                                 cudaMemcpyHostToDevice, e->stream));
     BDC_CUDA_TRY(cudaMemcpyAsync(e->inst, inst.data(), inst.size() * sizeof(double), cudaMemcpyHostToDevice,
                                  e->stream));
     BDC_CUDA_TRY(cudaMemsetAsync(e->counter, 0, (64 + 2 * (size_t)nd) * sizeof(uint32_t), e->stream));
@@ -525,6 +532,139 @@ extern "C" bdc_status bdc_ba_iterate(bdc_engine *e, int max_iters, double tol, i
     return st;
 }
 
+// ---------------------------------------------------------------------------
+// batches: several engines (different n, each with its d values) iterated by
+// one CUDA graph; each engine's kernels run on a stream forked from the
+// batch stream, so small instances overlap.
+// ---------------------------------------------------------------------------
+struct bdc_batch {
+    std::vector<bdc_engine *> engs;
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
+    cudaStream_t main = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int64_t graph_kernels[2] = {0, 0};
+    int chunk = 8;
+};
+
+extern "C" bdc_status bdc_batch_create(bdc_engine *const *engs, int count, int chunk, bdc_batch **out) {
+    if (!out || !engs || count < 1) BDC_FAIL(BDC_EINVAL, "bdc_batch_create: need engines");
+    *out = nullptr;
+    for (int i = 0; i < count; i++) {
+        if (!engs[i] || !engs[i]->bound) BDC_FAIL(BDC_ENOTBOUND, "bdc_batch_create: every engine must be bound");
+        if (engs[i]->stream != engs[0]->stream || engs[0]->stream == nullptr)
+            BDC_FAIL(BDC_EINVAL, "bdc_batch_create: engines must share one non-default stream");
+        for (int j = 0; j < i; j++)
+            if (engs[j] == engs[i]) BDC_FAIL(BDC_EINVAL, "bdc_batch_create: an engine appears twice");
+    }
+    bdc_batch *b = new bdc_batch();
+    b->engs.assign(engs, engs + count);
+    b->main = engs[0]->stream;
+    b->chunk = chunk < 1 ? 1 : chunk;
+    b->side.resize(count);
+    b->join.resize(count);
+    cudaError_t err = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    for (int i = 0; i < count && err == cudaSuccess; i++) {
+        err = cudaStreamCreateWithFlags(&b->side[i], cudaStreamNonBlocking);
+        if (err == cudaSuccess) err = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming);
+    }
+    if (err != cudaSuccess) {
+        bdc_set_error(std::string("bdc_batch_create: ") + cudaGetErrorString(err));
+        delete b;
+        return BDC_ECUDA;
+    }
+    *out = b;
+    return BDC_OK;
+}
+
+extern "C" void bdc_batch_destroy(bdc_batch *b) {
+    if (!b) return;
+    for (int p = 0; p < 2; p++)
+        if (b->graph[p]) cudaGraphExecDestroy(b->graph[p]);
+    for (size_t i = 0; i < b->side.size(); i++) {
+        if (b->side[i]) cudaStreamDestroy(b->side[i]);
+        if (b->join[i]) cudaEventDestroy(b->join[i]);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
+    delete b;
+}
+
+static bdc_status batch_graph(bdc_batch *b, int prec, cudaGraphExec_t *out) {
+    if (!b->graph[prec]) {
+        cudaGraph_t graph;
+        std::vector<int64_t> before(b->engs.size());
+        BDC_CUDA_TRY(cudaStreamBeginCapture(b->main, cudaStreamCaptureModeThreadLocal));
+        bdc_status st = BDC_OK;
+        cudaError_t ce = cudaEventRecord(b->fork, b->main);
+        for (size_t i = 0; i < b->engs.size() && st == BDC_OK && ce == cudaSuccess; i++) {
+            bdc_engine *e = b->engs[i];
+            ce = cudaStreamWaitEvent(b->side[i], b->fork, 0);
+            before[i] = e->launches;
+            e->stream = b->side[i];
+            for (int k = 0; k < b->chunk && st == BDC_OK; k++) st = iter_once(e, prec, BDC_SWEEP);
+            e->stream = b->main;
+            if (ce == cudaSuccess) ce = cudaEventRecord(b->join[i], b->side[i]);
+            if (ce == cudaSuccess) ce = cudaStreamWaitEvent(b->main, b->join[i], 0);
+        }
+        cudaError_t ce2 = cudaStreamEndCapture(b->main, &graph);
+        int64_t kernels = 0;
+        for (size_t i = 0; i < b->engs.size(); i++) {
+            kernels += b->engs[i]->launches - before[i];
+            b->engs[i]->launches = before[i];
+        }
+        if (st != BDC_OK) return st;
+        if (ce != cudaSuccess || ce2 != cudaSuccess)
+            BDC_FAIL(BDC_ECUDA, std::string("batch capture: ") + cudaGetErrorString(ce != cudaSuccess ? ce : ce2));
+        ce = cudaGraphInstantiate(&b->graph[prec], graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) {
+            b->graph[prec] = nullptr;
+            BDC_FAIL(BDC_ECUDA, std::string("batch instantiate: ") + cudaGetErrorString(ce));
+        }
+        b->graph_kernels[prec] = kernels;
+    }
+    *out = b->graph[prec];
+    return BDC_OK;
+}
+
+extern "C" bdc_status bdc_batch_iterate(bdc_batch *b, int max_iters, double tol, int prec, int *iters_launched) {
+    if (!b) BDC_FAIL(BDC_EINVAL, "bdc_batch_iterate: batch is NULL");
+    if (max_iters < 0 || (prec != BDC_FP32 && prec != BDC_FP64)) BDC_FAIL(BDC_EINVAL, "bdc_batch_iterate: bad arguments");
+    for (bdc_engine *e : b->engs) {
+        BDC_TRY(make_current(e, prec));
+        BDC_TRY(activate(e, tol));
+    }
+    cudaGraphExec_t g;
+    BDC_TRY(batch_graph(b, prec, &g));
+    int done = 0;
+    std::vector<double> h;
+    while (done < max_iters) {
+        BDC_CUDA_TRY(cudaGraphLaunch(g, b->main));
+        b->engs[0]->launches += b->graph_kernels[prec];
+        done += b->chunk;
+        if (tol >= 0.0 && done < max_iters) {
+            bool any = false;
+            for (bdc_engine *e : b->engs) {
+                BDC_TRY(read_inst(e, h));
+                for (int z = 0; z < e->nd; z++) any |= h[(size_t)z * INST_STRIDE + I_ACTIVE] != 0.0;
+            }
+            if (!any) break;
+        }
+    }
+    BDC_CUDA_TRY(cudaStreamSynchronize(b->main));
+    for (bdc_engine *e : b->engs) e->iters_total += done;
+    if (iters_launched) *iters_launched = done;
+    bdc_status st = BDC_OK;
+    for (bdc_engine *e : b->engs) {
+        BDC_TRY(read_inst(e, h));
+        for (int z = 0; z < e->nd; z++)
+            if (h[(size_t)z * INST_STRIDE + I_STATUS] != 0.0) st = BDC_ENONFINITE;
+    }
+    if (st != BDC_OK) bdc_set_error("bdc_batch_iterate: non-finite value in a reduction");
+    return st;
+}
+
 extern "C" bdc_status bdc_get_history(bdc_engine *e, int inst, double *lower, double *upper, int len, int *count) {
     if (!e || !e->bound) BDC_FAIL(BDC_ENOTBOUND, "bdc_get_history: no workspace bound");
     if (inst < 0 || inst >= e->nd || len < 0) BDC_FAIL(BDC_EINVAL, "bdc_get_history: bad instance or length");
@@ -625,8 +765,8 @@ extern "C" bdc_status bdc_certify_upper(bdc_engine *e, const double *q_dev, doub
     }
     BDC_CUDA_TRY(cudaGetLastError());
     BDC_TRY(sweep_adjoint<double>(e, b, Lsrc, b.omega, e->marg, MODE_CERT));
-    k_finalize_cert<<<(nd + 63) / 64, 64, 0, e->stream>>>(nd, b.part, maxblk, g0, b.s.nblk_cols, Kterms,
-                                                          q_dev ? 0 : 1, e->inst); e->launches++;
+    k_finalize_cert<<<nd, FIN_THREADS, 0, e->stream>>>(nd, b.part, maxblk, g0, b.s.nblk_cols, Kterms, q_dev ? 0 : 1,
+                                                       e->inst); e->launches++;
     BDC_CUDA_TRY(cudaGetLastError());
     std::vector<double> h;
     BDC_TRY(read_inst(e, h));
@@ -840,6 +980,110 @@ extern "C" bdc_status bdc_subseq_counts(int n, const uint64_t *x_dev, int64_t nx
 }
 
 extern "C" int64_t bdc_launch_count(const bdc_engine *e) { return e ? e->launches : 0; }
+
+extern "C" bdc_status bdc_get_schedule(const bdc_engine *e, int prec, int *n1, int *n2, int *width) {
+    if (!e || (prec != BDC_FP32 && prec != BDC_FP64)) BDC_FAIL(BDC_EINVAL, "bdc_get_schedule: bad arguments");
+    const Sched &s = (prec == BDC_FP32) ? e->f32.s : e->f64.s;
+    if (n1) *n1 = s.n1;
+    if (n2) *n2 = s.n2;
+    if (width) *width = 1 << s.lw;
+    return BDC_OK;
+}
+
+template <typename T>
+static bdc_status time_sweeps(bdc_engine *e, PrecBuf<T> &b, int reps, float *ms) {
+    cudaEvent_t a, z;
+    BDC_CUDA_TRY(cudaEventCreate(&a));
+    BDC_CUDA_TRY(cudaEventCreate(&z));
+    bdc_status st = BDC_OK;
+    // one untimed pass (first touch), then `reps` timed forward + adjoint sweeps;
+    // no update is applied, D is overwritten (the caller materialised p first)
+    for (int r = 0; r <= reps && st == BDC_OK; r++) {
+        if (r == 1) cudaEventRecord(a, e->stream);
+        st = sweep_forward<T>(e, b, b.p, 0, MODE_ITER);
+        if (st == BDC_OK) st = sweep_adjoint<T>(e, b, b.L, b.omega, b.D, MODE_ITER);
+    }
+    cudaEventRecord(z, e->stream);
+    cudaError_t err = cudaEventSynchronize(z);
+    if (st == BDC_OK && err == cudaSuccess) err = cudaEventElapsedTime(ms, a, z);
+    cudaEventDestroy(a);
+    cudaEventDestroy(z);
+    if (st != BDC_OK) return st;
+    if (err != cudaSuccess) BDC_FAIL(BDC_ECUDA, std::string("autotune timing: ") + cudaGetErrorString(err));
+    *ms /= reps;
+    return BDC_OK;
+}
+
+template <typename T>
+static bdc_status autotune_impl(bdc_engine *e, PrecBuf<T> &b, int prec, int reps, double *best_ms) {
+    const int n = e->n;
+    const size_t tile = (sizeof(T) == 4) ? 32768 : 16384;
+    Sched best = b.s;
+    float best_t = 1e30f;
+    std::vector<Sched> cands;
+    if (n <= 14) {  // one in-CTA pass; the split buffers are not reserved below n = 15
+        if (best_ms) *best_ms = 0.0;
+        return BDC_OK;
+    }
+    for (int n2 = std::max(8, n - 14); n2 <= std::min(n - 1, (sizeof(T) == 4) ? 14 : 13); n2++) {
+        const int n1 = n - n2;
+        for (int lw = 0; lw <= std::min(5, n2); lw++) {
+            if (((size_t)2 << n1 << lw) > tile) break;
+            Sched s{};
+            s.n1 = n1;
+            s.n2 = n2;
+            s.lw = lw;
+            s.nblk_cols = 1 << (n2 - lw);
+            cands.push_back(s);
+        }
+    }
+    for (const Sched &s : cands) {
+        if (s.nblk_cols > part_maxblk(e)) continue;
+        b.s = s;
+        float t = 0.f;
+        BDC_TRY(time_sweeps<T>(e, b, reps, &t));
+        if (t < best_t) {
+            best_t = t;
+            best = s;
+        }
+    }
+    b.s = best;
+    for (int impl = 0; impl < 2; impl++)
+        if (e->graph[prec][impl]) {
+            cudaGraphExecDestroy(e->graph[prec][impl]);
+            e->graph[prec][impl] = nullptr;
+        }
+    if (best_ms) *best_ms = best_t;
+    return BDC_OK;
+}
+
+extern "C" bdc_status bdc_autotune(bdc_engine *e, int prec, int reps, int n2, int width, double *best_ms) {
+    if (!e || !e->bound) BDC_FAIL(BDC_ENOTBOUND, "bdc_autotune: no workspace bound");
+    if ((prec != BDC_FP32 && prec != BDC_FP64) || reps < 1) BDC_FAIL(BDC_EINVAL, "bdc_autotune: bad arguments");
+    BDC_TRY(make_current(e, prec));
+    BDC_TRY(materialize(e));
+    BDC_TRY(activate(e, -1.0));
+    if (n2 > 0) {
+        // set a known schedule (e.g. from a cache) instead of searching
+        Sched s = make_sched(e->n, prec == BDC_FP32 ? 4 : 8, n2, width);
+        const size_t tile = (prec == BDC_FP32) ? 32768 : 16384;
+        if (e->n < 15 || s.n2 < 8 || s.n2 > 14 || ((size_t)2 << s.n1 << s.lw) > tile || s.nblk_cols > part_maxblk(e))
+            BDC_FAIL(BDC_EINVAL, "bdc_autotune: schedule outside the reserved buffers (n >= 15, 8 <= n2 <= 14, tile)");
+        PrecBuf<float> &f = e->f32;
+        PrecBuf<double> &d = e->f64;
+        if (prec == BDC_FP32) f.s = s;
+        else d.s = s;
+        for (int impl = 0; impl < 2; impl++)
+            if (e->graph[prec][impl]) {
+                cudaGraphExecDestroy(e->graph[prec][impl]);
+                e->graph[prec][impl] = nullptr;
+            }
+        if (best_ms) *best_ms = 0.0;
+        return BDC_OK;
+    }
+    if (prec == BDC_FP32) return autotune_impl<float>(e, e->f32, prec, reps, best_ms);
+    return autotune_impl<double>(e, e->f64, prec, reps, best_ms);
+}
 
 extern "C" bdc_status bdc_profile_iteration(bdc_engine *e, int prec, int impl, int reps, double *stage_ms,
                                             char *names, int names_len, int *nstages) {

@@ -32,9 +32,15 @@ __device__ __forceinline__ uint32_t warp_excl_scan(uint32_t v, int lane) {
     return s - v;
 }
 
-__device__ __forceinline__ double clog2c(uint32_t c, const double *__restrict__ tab) {
-    if (tab != nullptr && c < 4096u) return __ldg(tab + c);
-    return c <= 1u ? 0.0 : (double)c * log2((double)c);
+// c*log2(c) in fixed point with 34 fractional bits: sum_{|y|=k} Count log2 Count
+// <= C(n,k) log2 C(n,k) < 2^29 for n <= 26, so an int64 sum never overflows and
+// the accumulation needs no floating point (FP64 issue is scarce on B300).
+// Table entries (c < 65536) are host-rounded from long double; larger counts
+// are rounded from FP64 here.
+constexpr double FIX_SCALE = 17179869184.0;  // 2^34
+__device__ __forceinline__ long long clog2c_fix(uint32_t c, const long long *__restrict__ tab) {
+    if (tab != nullptr && c < 65536u) return __ldg(tab + c);
+    return c <= 1u ? 0ll : llrint((double)c * log2((double)c) * FIX_SCALE);
 }
 
 // ---------------------------------------------------------------------------
@@ -159,7 +165,7 @@ struct WalkArgs {
     uint32_t *counter;          // dynamic work counter (may be null: static)
     // WALK_STATS
     uint32_t *Nk32; uint64_t *Nk64; double *Sk; int stride;
-    const double *tab;          // c*log2(c) for c < 4096
+    const long long *tabfix;    // c*log2(c)*2^34 for c < 65536
     const double *tab_log2;     // log2(c) for c < 4096
     // WALK_LITERAL_D
     const double *L;            // [nd][2^(n+1)] log2 q_k
@@ -202,7 +208,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
         // per-lane accumulators: lane k owns length k (stats) / a 32-slot
         // gather buffer (literal D)
         uint32_t accN = (lane == 0) ? 1u : 0u;
-        double accS = 0.0;
+        long long accS = 0;
         double accD = 0.0;
         uint32_t bcode = 0, bcnt = 0;
         int nbuf = 0;
@@ -233,7 +239,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
             int k = bitlen32(code) - 1;
             // record (code, k, cnt)
             if (MODE == WALK_STATS) {
-                if (lane == k) { accN++; accS += clog2c(cnt, a.tab); }
+                if (lane == k) { accN++; accS += clog2c_fix(cnt, a.tabfix); }
             } else if (MODE == WALK_EMIT) {
                 if (lane == 0) a.emb[code] = cnt;
             } else {
@@ -266,7 +272,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
             if (lane <= n) {
                 if (a.Nk32) a.Nk32[item * a.stride + lane] = accN;
                 if (a.Nk64) a.Nk64[item * a.stride + lane] = accN;
-                if (a.Sk) a.Sk[item * a.stride + lane] = accS;
+                if (a.Sk) a.Sk[item * a.stride + lane] = (double)accS * (1.0 / FIX_SCALE);
             }
         } else if (MODE == WALK_LITERAL_D) {
             if (lane < nbuf) {
@@ -486,7 +492,7 @@ bdc_status launch_subseq_stats(bdc_engine *e) {
     a.Nk32 = e->Nk;
     a.Sk = e->Sk;
     a.stride = e->n + 1;
-    a.tab = e->tab_clog;
+    a.tabfix = e->tab_fix;
     BDC_CUDA_TRY(cudaMemsetAsync(e->counter, 0, 64 * sizeof(uint32_t), e->stream));
     k_subseq_walk<WALK_STATS><<<walk_grid(), WARPS_PER_CTA * 32, 0, e->stream>>>(a); e->launches++;
     BDC_CUDA_TRY(cudaGetLastError());
@@ -585,7 +591,7 @@ bdc_status launch_literal_q(bdc_engine *e) {
 // test hook
 // ---------------------------------------------------------------------------
 bdc_status subseq_counts_impl(int n, const uint64_t *x_dev, int64_t nx, uint64_t *N_dev, double *S_dev,
-                              uint64_t *emb_dev, cudaStream_t st, const double *tab_clog) {
+                              uint64_t *emb_dev, cudaStream_t st, const long long *tab_fix) {
     WalkArgs a{};
     a.n = n;
     a.count = nx;
@@ -593,7 +599,7 @@ bdc_status subseq_counts_impl(int n, const uint64_t *x_dev, int64_t nx, uint64_t
     a.Nk64 = N_dev;
     a.Sk = S_dev;
     a.stride = n + 1;
-    a.tab = tab_clog;
+    a.tabfix = tab_fix;
     int grid = (int)std::min<int64_t>((nx + WARPS_PER_CTA - 1) / WARPS_PER_CTA, walk_grid());
     if (grid < 1) grid = 1;
     k_subseq_walk<WALK_STATS><<<grid, WARPS_PER_CTA * 32, 0, st>>>(a);

@@ -30,83 +30,332 @@
 namespace {
 
 constexpr int SW_THREADS = 512;
-constexpr int SW_R = 16;
 
 // forward sweep of nn symbols over a tile of (2 << nn) rows x (1 << lw)
 // columns held in shared memory (rows >= 2^nn hold the input, rows < 2^nn
-// start at zero).  Rows are updated in increasing order, chunk by chunk:
-// a row only reads rows >= itself, so one barrier per chunk is enough.
-template <typename T>
-__device__ void lsweep_fwd(T *buf, int nn, int lw) {
+// start at zero).  Thread t owns the elements e = t + j*SW_THREADS (j < R) of
+// the bottom half for the whole sweep and keeps their values in registers;
+// per step it reads the two inserted-bit rows from shared memory, then
+// (after a barrier) publishes its new values.  R is a compile-time bound
+// on the elements per thread: R * SW_THREADS >= 2^nn << lw.
+template <typename T, int R>
+__device__ void lsweep_fwd_reg(T *buf, int nn, int lw) {
     const int tid = threadIdx.x;
+    const uint32_t nel = (1u << nn) << lw;
+    const uint32_t cmask = (1u << lw) - 1u;
+    T own[R];
+#pragma unroll
+    for (int j = 0; j < R; j++) {
+        uint32_t e = tid + j * SW_THREADS;
+        own[j] = (e < nel) ? buf[e] : (T)0;
+    }
     for (int i = 0; i < nn; i++) {
         const int m = nn - i - 1;
         const uint32_t row_lo = 1u << m;
-        const uint32_t nel = ((1u << nn) - row_lo) << lw;
-        const uint32_t cmask = (1u << lw) - 1u;
-        for (uint32_t base = 0; base < nel; base += SW_THREADS * SW_R) {
-            T v[SW_R];
+        // read phase: other rows' old values from shared memory, own in registers
 #pragma unroll
-            for (int r = 0; r < SW_R; r++) {
-                uint32_t e = base + r * SW_THREADS + tid;
-                if (e < nel) {
-                    uint32_t P = row_lo + (e >> lw);
-                    uint32_t c = e & cmask;
-                    uint32_t i0 = ((P >> m) << (m + 1)) | (P & (row_lo - 1u));
-                    v[r] = buf[(P << lw) | c] + buf[(i0 << lw) | c] + buf[((i0 | row_lo) << lw) | c];
+        for (int j = 0; j < R; j++) {
+            uint32_t e = tid + j * SW_THREADS;
+            uint32_t P = e >> lw;
+            if (e < nel && P >= row_lo) {
+                uint32_t c = e & cmask;
+                uint32_t i0 = ((P >> m) << (m + 1)) | (P & (row_lo - 1u));
+                own[j] += buf[(i0 << lw) | c] + buf[((i0 | row_lo) << lw) | c];
+            }
+        }
+        __syncthreads();
+        // publish phase
+#pragma unroll
+        for (int j = 0; j < R; j++) {
+            uint32_t e = tid + j * SW_THREADS;
+            if (e < nel && (e >> lw) >= row_lo) buf[e] = own[j];
+        }
+        __syncthreads();
+    }
+}
+
+// adjoint sweep: every row Q >= 2^(m+1) adds the row cmp(Q) (bit m removed)
+// of the previous level.  Thread t owns e = t + j*SW_THREADS of the whole
+// tile (R * SW_THREADS >= 2^(nn+1) << lw); afterwards rows [2^nn, 2^(nn+1))
+// hold the result.
+template <typename T, int R>
+__device__ void lsweep_adj_reg(T *buf, int nn, int lw) {
+    const int tid = threadIdx.x;
+    const uint32_t nel = (2u << nn) << lw;
+    const uint32_t cmask = (1u << lw) - 1u;
+    T own[R];
+#pragma unroll
+    for (int j = 0; j < R; j++) {
+        uint32_t e = tid + j * SW_THREADS;
+        own[j] = (e < nel) ? buf[e] : (T)0;
+    }
+    for (int i = nn - 1; i >= 0; i--) {
+        const int m = nn - i - 1;
+        const uint32_t row_lo = 2u << m;
+        const uint32_t lomask = (1u << m) - 1u;
+#pragma unroll
+        for (int j = 0; j < R; j++) {
+            uint32_t e = tid + j * SW_THREADS;
+            uint32_t Q = e >> lw;
+            if (e < nel && Q >= row_lo) {
+                uint32_t cq = ((Q >> (m + 1)) << m) | (Q & lomask);
+                own[j] += buf[(cq << lw) | (e & cmask)];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < R; j++) {
+            uint32_t e = tid + j * SW_THREADS;
+            if (e < nel && (e >> lw) >= row_lo) buf[e] = own[j];
+        }
+        __syncthreads();
+    }
+}
+
+// dispatch on the tile size (elements per thread rounded up to a power of 2)
+// ---------------------------------------------------------------------------
+// 4-wide variants: a thread owns groups of 4 consecutive elements (4 columns of
+// one row when the tile is at least 4 columns wide, 4 consecutive rows of a
+// one-column tile), so one index computation and two 16-byte shared loads
+// serve 4 elements.  Same arithmetic, in the same order, as the scalar forms.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void ld4(const float *p, float *v) {
+    float4 t = *reinterpret_cast<const float4 *>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double *p, double *v) {
+    double2 a = *reinterpret_cast<const double2 *>(p), b = *reinterpret_cast<const double2 *>(p + 2);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void st4(float *p, const float *v) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double *p, const double *v) {
+    *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+    *reinterpret_cast<double2 *>(p + 2) = make_double2(v[2], v[3]);
+}
+__device__ __forceinline__ void ld2(const float *p, float *v) {
+    float2 t = *reinterpret_cast<const float2 *>(p);
+    v[0] = t.x; v[1] = t.y;
+}
+__device__ __forceinline__ void ld2(const double *p, double *v) {
+    double2 t = *reinterpret_cast<const double2 *>(p);
+    v[0] = t.x; v[1] = t.y;
+}
+
+// forward, tile of >= 4 columns (lw >= 2): group g = 4 columns of row (4g) >> lw
+template <typename T, int G>
+__device__ void lsweep_fwd_cols4(T *buf, int nn, int lw) {
+    const int tid = threadIdx.x;
+    const uint32_t ng = ((1u << nn) << lw) >> 2;
+    const uint32_t cmask = (1u << lw) - 1u;
+    T own[G][4];
+#pragma unroll
+    for (int j = 0; j < G; j++) {
+        uint32_t g = tid + j * SW_THREADS;
+        if (g < ng) ld4(buf + 4 * g, own[j]);
+    }
+    for (int i = 0; i < nn; i++) {
+        const int m = nn - i - 1;
+        const uint32_t row_lo = 1u << m;
+#pragma unroll
+        for (int j = 0; j < G; j++) {
+            uint32_t g = tid + j * SW_THREADS;
+            uint32_t e = 4 * g, P = e >> lw;
+            if (g < ng && P >= row_lo) {
+                uint32_t c = e & cmask;
+                uint32_t i0 = ((P >> m) << (m + 1)) | (P & (row_lo - 1u));
+                T a[4], b[4];
+                ld4(buf + ((i0 << lw) | c), a);
+                ld4(buf + (((i0 | row_lo) << lw) | c), b);
+#pragma unroll
+                for (int k = 0; k < 4; k++) own[j][k] = own[j][k] + a[k] + b[k];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < G; j++) {
+            uint32_t g = tid + j * SW_THREADS;
+            if (g < ng && ((4 * g) >> lw) >= row_lo) st4(buf + 4 * g, own[j]);
+        }
+        __syncthreads();
+    }
+}
+
+// forward, one-column tile (lw == 0): group g = rows 4g..4g+3 (nn >= 2)
+template <typename T, int G>
+__device__ void lsweep_fwd_rows4(T *buf, int nn) {
+    const int tid = threadIdx.x;
+    const uint32_t ng = (1u << nn) >> 2;
+    T own[G][4];
+#pragma unroll
+    for (int j = 0; j < G; j++) {
+        uint32_t g = tid + j * SW_THREADS;
+        if (g < ng) ld4(buf + 4 * g, own[j]);
+    }
+    for (int i = 0; i < nn; i++) {
+        const int m = nn - i - 1;
+        const uint32_t row_lo = 1u << m;
+#pragma unroll
+        for (int j = 0; j < G; j++) {
+            uint32_t g = tid + j * SW_THREADS;
+            uint32_t P0 = 4 * g;
+            if (g < ng && P0 + 3 >= row_lo) {
+                T v[8];
+                if (m >= 2) {
+                    uint32_t i0 = ((P0 >> m) << (m + 1)) | (P0 & (row_lo - 1u));
+                    ld4(buf + i0, v);
+                    ld4(buf + (i0 | row_lo), v + 4);
+#pragma unroll
+                    for (int k = 0; k < 4; k++) own[j][k] = own[j][k] + v[k] + v[4 + k];
+                } else {
+                    // rows 2*P0 .. 2*P0+7 hold both inserted-bit rows of all four
+                    ld4(buf + 2 * P0, v);
+                    ld4(buf + 2 * P0 + 4, v + 4);
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        if (P0 + k < row_lo) continue;
+                        // m == 1: i0 = 8g + 4(k>>1) + (k&1), i1 = i0 + 2 ; m == 0: i0 = 8g + 2k, i1 = i0 + 1
+                        int i0 = (m == 1) ? (4 * (k >> 1) + (k & 1)) : 2 * k;
+                        int i1 = (m == 1) ? i0 + 2 : i0 + 1;
+                        own[j][k] = own[j][k] + v[i0] + v[i1];
+                    }
                 }
             }
-            __syncthreads();
+        }
+        __syncthreads();
 #pragma unroll
-            for (int r = 0; r < SW_R; r++) {
-                uint32_t e = base + r * SW_THREADS + tid;
-                if (e < nel) {
-                    uint32_t P = row_lo + (e >> lw);
-                    buf[(P << lw) | (e & cmask)] = v[r];
-                }
+        for (int j = 0; j < G; j++) {
+            uint32_t g = tid + j * SW_THREADS;
+            uint32_t P0 = 4 * g;
+            if (g < ng && P0 + 3 >= row_lo) {
+                if (P0 >= row_lo) st4(buf + P0, own[j]);
+                else
+                    for (int k = 0; k < 4; k++)
+                        if (P0 + k >= row_lo) buf[P0 + k] = own[j][k];
             }
         }
         __syncthreads();
     }
 }
 
-// adjoint sweep: rows Q >= 2^(m+1) updated in decreasing order (a row only
-// reads rows <= itself).  Afterwards rows [2^nn, 2^(nn+1)) hold the result.
-template <typename T>
-__device__ void lsweep_adj(T *buf, int nn, int lw) {
+// adjoint, tile of >= 4 columns
+template <typename T, int G>
+__device__ void lsweep_adj_cols4(T *buf, int nn, int lw) {
     const int tid = threadIdx.x;
+    const uint32_t ng = ((2u << nn) << lw) >> 2;
+    const uint32_t cmask = (1u << lw) - 1u;
+    T own[G][4];
+#pragma unroll
+    for (int j = 0; j < G; j++) {
+        uint32_t g = tid + j * SW_THREADS;
+        if (g < ng) ld4(buf + 4 * g, own[j]);
+    }
     for (int i = nn - 1; i >= 0; i--) {
         const int m = nn - i - 1;
         const uint32_t row_lo = 2u << m;
-        const uint32_t top = (2u << nn) - 1u;
-        const uint32_t nel = ((2u << nn) - row_lo) << lw;
-        const uint32_t cmask = (1u << lw) - 1u;
         const uint32_t lomask = (1u << m) - 1u;
-        for (uint32_t base = 0; base < nel; base += SW_THREADS * SW_R) {
-            T v[SW_R];
 #pragma unroll
-            for (int r = 0; r < SW_R; r++) {
-                uint32_t e = base + r * SW_THREADS + tid;
-                if (e < nel) {
-                    uint32_t Q = top - (e >> lw);
-                    uint32_t c = e & cmask;
-                    uint32_t cq = ((Q >> (m + 1)) << m) | (Q & lomask);
-                    v[r] = buf[(Q << lw) | c] + buf[(cq << lw) | c];
+        for (int j = 0; j < G; j++) {
+            uint32_t g = tid + j * SW_THREADS;
+            uint32_t e = 4 * g, Q = e >> lw;
+            if (g < ng && Q >= row_lo) {
+                uint32_t cq = ((Q >> (m + 1)) << m) | (Q & lomask);
+                T a[4];
+                ld4(buf + ((cq << lw) | (e & cmask)), a);
+#pragma unroll
+                for (int k = 0; k < 4; k++) own[j][k] = own[j][k] + a[k];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < G; j++) {
+            uint32_t g = tid + j * SW_THREADS;
+            if (g < ng && ((4 * g) >> lw) >= row_lo) st4(buf + 4 * g, own[j]);
+        }
+        __syncthreads();
+    }
+}
+
+// adjoint, one-column tile (nn >= 1): group g = rows 4g..4g+3
+template <typename T, int G>
+__device__ void lsweep_adj_rows4(T *buf, int nn) {
+    const int tid = threadIdx.x;
+    const uint32_t ng = (2u << nn) >> 2;
+    T own[G][4];
+#pragma unroll
+    for (int j = 0; j < G; j++) {
+        uint32_t g = tid + j * SW_THREADS;
+        if (g < ng) ld4(buf + 4 * g, own[j]);
+    }
+    for (int i = nn - 1; i >= 0; i--) {
+        const int m = nn - i - 1;
+        const uint32_t row_lo = 2u << m;
+        const uint32_t lomask = (1u << m) - 1u;
+#pragma unroll
+        for (int j = 0; j < G; j++) {
+            uint32_t g = tid + j * SW_THREADS;
+            uint32_t Q0 = 4 * g;
+            if (g < ng && Q0 + 3 >= row_lo) {
+                if (m >= 2) {
+                    uint32_t cq = ((Q0 >> (m + 1)) << m) | (Q0 & lomask);
+                    T a[4];
+                    ld4(buf + cq, a);
+#pragma unroll
+                    for (int k = 0; k < 4; k++) own[j][k] = own[j][k] + a[k];
+                } else {
+                    // m == 1: cmp = 2g, 2g+1, 2g, 2g+1 ; m == 0: cmp = 2g, 2g, 2g+1, 2g+1
+                    T a[2];
+                    ld2(buf + 2 * g, a);
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        if (Q0 + k < row_lo) continue;
+                        own[j][k] = own[j][k] + a[(m == 1) ? (k & 1) : (k >> 1)];
+                    }
                 }
             }
-            __syncthreads();
+        }
+        __syncthreads();
 #pragma unroll
-            for (int r = 0; r < SW_R; r++) {
-                uint32_t e = base + r * SW_THREADS + tid;
-                if (e < nel) {
-                    uint32_t Q = top - (e >> lw);
-                    buf[(Q << lw) | (e & cmask)] = v[r];
-                }
+        for (int j = 0; j < G; j++) {
+            uint32_t g = tid + j * SW_THREADS;
+            uint32_t Q0 = 4 * g;
+            if (g < ng && Q0 + 3 >= row_lo) {
+                if (Q0 >= row_lo) st4(buf + Q0, own[j]);
+                else
+                    for (int k = 0; k < 4; k++)
+                        if (Q0 + k >= row_lo) buf[Q0 + k] = own[j][k];
             }
         }
         __syncthreads();
     }
 }
+
+// choose the form: R = elements per thread (power of two).  R >= 4 and a tile
+// of >= 4 columns or one column use the 4-wide forms; otherwise scalar.
+template <typename T, int R>
+__device__ __forceinline__ void lsweep_fwd_any(T *buf, int nn, int lw) {
+    if constexpr (R >= 4) {
+        if (lw >= 2) { lsweep_fwd_cols4<T, R / 4>(buf, nn, lw); return; }
+        if (lw == 0 && nn >= 2) { lsweep_fwd_rows4<T, R / 4>(buf, nn); return; }
+    }
+    lsweep_fwd_reg<T, R>(buf, nn, lw);
+}
+
+template <typename T, int R>
+__device__ __forceinline__ void lsweep_adj_any(T *buf, int nn, int lw) {
+    if constexpr (R >= 4) {
+        if (lw >= 2) { lsweep_adj_cols4<T, R / 4>(buf, nn, lw); return; }
+        if (lw == 0 && nn >= 1) { lsweep_adj_rows4<T, R / 4>(buf, nn); return; }
+    }
+    lsweep_adj_reg<T, R>(buf, nn, lw);
+}
+
+// largest per-thread element count a tile can need (32K FP32 / 16K FP64 elements)
+template <typename T>
+constexpr int rmax_fwd() { return (sizeof(T) == 4 ? 32768 : 16384) / 2 / SW_THREADS; }
+template <typename T>
+constexpr int rmax_adj() { return (sizeof(T) == 4 ? 32768 : 16384) / SW_THREADS; }
 
 template <typename T>
 __device__ __forceinline__ double block_sum(double v, double *red) {
@@ -151,7 +400,7 @@ struct SweepArgs {
 // Prologue applies the pending BA update p <- p 2^{Dbar - shift} and writes
 // p back.  With n2 == 0 the pass covers all n symbols and writes q, L.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, int R>
 __global__ void __launch_bounds__(SW_THREADS) k_cols_fwd(SweepArgs a, T *p, const T *D, T *F1, T *q, T *L,
                                                           int apply_update, int mode) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -168,7 +417,7 @@ __global__ void __launch_bounds__(SW_THREADS) k_cols_fwd(SweepArgs a, T *p, cons
     const bool upd = apply_update && inst[I_PENDING] != 0.0;
     const T shift = (T)inst[I_SHIFT];
     const uint32_t ntop = (1u << n1) << lw;
-    double psum = 0.0;
+    T psum = (T)0;  // per-thread partial in the working precision, block sum in FP64
     for (uint32_t e = threadIdx.x; e < ntop; e += SW_THREADS) {
         uint32_t x1 = e >> lw, c = e & (w - 1u);
         size_t x = ((size_t)x1 << n2) | (col0 + c);
@@ -179,15 +428,15 @@ __global__ void __launch_bounds__(SW_THREADS) k_cols_fwd(SweepArgs a, T *p, cons
         }
         buf[ntop + e] = v;
         buf[e] = (T)0;
-        psum += (double)v;
+        psum += v;
     }
-    double s = block_sum<T>(psum, red);
+    double s = block_sum<T>((double)psum, red);
     if (threadIdx.x == 0 && (mode == MODE_ITER || mode == MODE_DIV)) {
         double *pp = a.part + ((size_t)z * 2 + 0) * a.maxblk * 4 + blockIdx.x * 4;
         pp[0] = s;
     }
     __syncthreads();
-    lsweep_fwd<T>(buf, n1, lw);
+    lsweep_fwd_any<T, R>(buf, n1, lw);
     if (n2 > 0) {
         T *Fz = F1 + z * a.strideN;
         for (uint32_t e = threadIdx.x + w; e < ntop; e += SW_THREADS) {
@@ -207,7 +456,7 @@ __global__ void __launch_bounds__(SW_THREADS) k_cols_fwd(SweepArgs a, T *p, cons
 
 // pass 2 forward (rows): one row c1 per CTA; input row = F1[c1] (c1 < 2^n1)
 // or p[x1 = c1 - 2^n1]; output codes c2 < 32 go to the transposed Ts.
-template <typename T>
+template <typename T, int R>
 __global__ void __launch_bounds__(SW_THREADS) k_rows_fwd(SweepArgs a, const T *p, const T *F1, T *Tm, T *Ts) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *buf = reinterpret_cast<T *>(smem_raw);
@@ -223,7 +472,7 @@ __global__ void __launch_bounds__(SW_THREADS) k_rows_fwd(SweepArgs a, const T *p
         buf[e] = (T)0;
     }
     __syncthreads();
-    lsweep_fwd<T>(buf, n2, 0);
+    lsweep_fwd_any<T, R>(buf, n2, 0);
     T *Tmz = Tm + z * a.strideM;
     T *Tsz = Ts + z * ((size_t)32 << (n1 + 1));
     for (uint32_t c2 = threadIdx.x + 1; c2 < half; c2 += SW_THREADS) {
@@ -267,7 +516,7 @@ __global__ void k_combine(SweepArgs a, const T *p, const T *F1, const T *Tm, con
 
 // pass 2 adjoint (rows): gather omega_k L(code c1 . c2) over the row, adjoint
 // sweep over x2, write the row's top half to Gb[c1][x2].
-template <typename T>
+template <typename T, int R>
 __global__ void __launch_bounds__(SW_THREADS) k_rows_adj(SweepArgs a, const T *Lsrc, const T *omega, T *Gb) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *buf = reinterpret_cast<T *>(smem_raw);
@@ -288,7 +537,7 @@ __global__ void __launch_bounds__(SW_THREADS) k_rows_adj(SweepArgs a, const T *L
         buf[c2] = v;
     }
     __syncthreads();
-    lsweep_adj<T>(buf, n2, 0);
+    lsweep_adj_any<T, R>(buf, n2, 0);
     T *Gz = Gb + z * a.strideM + ((size_t)c1 << n2);
     const uint32_t half = 1u << n2;
     for (uint32_t e = threadIdx.x; e < half; e += SW_THREADS) Gz[e] = buf[half + e];
@@ -306,7 +555,7 @@ struct EpiArgs {
 
 // pass 1 adjoint (columns): load Gb (or omega L directly when n2 == 0), adjoint
 // sweep over x1, then the epilogue D_x = -Hb(x) - G(x) and block partials.
-template <typename T>
+template <typename T, int R>
 __global__ void __launch_bounds__(SW_THREADS) k_cols_adj(SweepArgs a, EpiArgs ep, const T *Gb, const T *Lsrc,
                                                           const T *omega, int mode) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -332,11 +581,12 @@ __global__ void __launch_bounds__(SW_THREADS) k_cols_adj(SweepArgs a, EpiArgs ep
             buf[c] = c ? om[bitlen32(c) - 1] * Lz[c] : (T)0;
     }
     __syncthreads();
-    lsweep_adj<T>(buf, n1, lw);
+    lsweep_adj_any<T, R>(buf, n1, lw);
     const T *Hbz = reinterpret_cast<const T *>(ep.Hb) + z * a.strideN;
     const T *pz = reinterpret_cast<const T *>(ep.p) + z * a.strideN;
     const uint32_t ntop = (1u << n1) << lw;
     double sZ = 0.0, mD = -INFINITY, sP = 0.0, mP = -INFINITY;
+    T tZ = (T)0, tM = (T)-INFINITY;  // MODE_ITER partials in the working precision
     const double add = (mode == MODE_DIV) ? inst[I_SUMP] : 0.0;
     for (uint32_t e = threadIdx.x; e < ntop; e += SW_THREADS) {
         uint32_t x1 = e >> lw, c = e & (w - 1u);
@@ -346,9 +596,8 @@ __global__ void __launch_bounds__(SW_THREADS) k_cols_adj(SweepArgs a, EpiArgs ep
         if (mode == MODE_ITER) {
             T Dv = -hb - G;
             reinterpret_cast<T *>(ep.Dout)[z * a.strideN + x] = Dv;
-            double pv = (double)pz[x];
-            sZ += pv * (double)exp2_t<T>(Dv);
-            mD = fmax(mD, (double)Dv);
+            tZ += pz[x] * exp2_t<T>(Dv);
+            tM = Dv > tM ? Dv : tM;
         } else if (mode == MODE_DIV) {
             double Dv = (double)(-hb - G) + add;
             reinterpret_cast<double *>(ep.Dout)[z * a.strideN + x] = Dv;
@@ -375,6 +624,10 @@ __global__ void __launch_bounds__(SW_THREADS) k_cols_adj(SweepArgs a, EpiArgs ep
             mD = fmax(mD, up);
             mP = fmax(mP, Dv);
         }
+    }
+    if (mode == MODE_ITER) {
+        sZ = (double)tZ;
+        mD = (double)tM;
     }
     double s1 = block_sum<T>(sZ, red);
     double s3 = block_sum<T>(sP, red);
@@ -418,6 +671,29 @@ cudaError_t allow_smem(K kernel, size_t bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// elements per thread of a tile, rounded up to a power of two
+inline int r_of(size_t elems) {
+    size_t per = (elems + SW_THREADS - 1) / SW_THREADS;
+    int r = 1;
+    while ((size_t)r < per) r <<= 1;
+    return r;
+}
+
+// run BODY with the compile-time constant R equal to the runtime value rv
+// (rv a power of two in [1, RMAX]); BODY sees `R`.
+#define SW_WITH_R(RMAX, rv, BODY)                                                             \
+    do {                                                                                      \
+        switch (rv) {                                                                         \
+            case 1: { constexpr int R = 1; BODY; } break;                                     \
+            case 2: { constexpr int R = 2; BODY; } break;                                     \
+            case 4: { constexpr int R = 4; BODY; } break;                                     \
+            case 8: { constexpr int R = 8; BODY; } break;                                     \
+            case 16: { constexpr int R = (16 <= (RMAX) ? 16 : (RMAX)); BODY; } break;         \
+            case 32: { constexpr int R = (32 <= (RMAX) ? 32 : (RMAX)); BODY; } break;         \
+            default: { constexpr int R = (RMAX); BODY; } break;                               \
+        }                                                                                     \
+    } while (0)
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -435,7 +711,9 @@ Sched make_sched(int n, int elem_bytes, int n2_override, int w_override) {
         s.nblk_cols = 1;
         return s;
     }
-    int n2max = nsingle;
+    // rows pass: 2^(n2+1) elements per CTA; 16K keeps the FP32 rows tile at
+    // 64 KB (several CTAs per SM) and every thread's elements in registers
+    int n2max = 13;
     int n2 = n2_override ? n2_override : std::min(n - 1, n2max);
     if (n2 < 5) n2 = std::min(5, n - 1);
     s.n2 = n2;
@@ -452,14 +730,28 @@ Sched make_sched(int n, int elem_bytes, int n2_override, int w_override) {
 }
 
 template <typename T>
-bdc_status sweep_prepare(bdc_engine *e, PrecBuf<T> &b) {
-    BDC_CUDA_TRY(allow_smem(k_cols_fwd<T>, tile_bytes_cols<T>(b.s)));
-    BDC_CUDA_TRY(allow_smem(k_cols_adj<T>, tile_bytes_cols<T>(b.s)));
-    if (b.s.n2 > 0) {
-        BDC_CUDA_TRY(allow_smem(k_rows_fwd<T>, tile_bytes_rows<T>(b.s)));
-        BDC_CUDA_TRY(allow_smem(k_rows_adj<T>, tile_bytes_rows<T>(b.s)));
+cudaError_t prepare_all(size_t cols_bytes, size_t rows_bytes) {
+    cudaError_t err = cudaSuccess;
+#define PREP_ONE(RR)                                                                                             \
+    if (RR <= rmax_fwd<T>()) {                                                                                   \
+        if (err == cudaSuccess) err = allow_smem(k_cols_fwd<T, (RR <= rmax_fwd<T>() ? RR : 1)>, cols_bytes);    \
+        if (err == cudaSuccess) err = allow_smem(k_rows_fwd<T, (RR <= rmax_fwd<T>() ? RR : 1)>, rows_bytes);    \
+    }                                                                                                            \
+    if (RR <= rmax_adj<T>()) {                                                                                   \
+        if (err == cudaSuccess) err = allow_smem(k_cols_adj<T, (RR <= rmax_adj<T>() ? RR : 1)>, cols_bytes);    \
+        if (err == cudaSuccess) err = allow_smem(k_rows_adj<T, (RR <= rmax_adj<T>() ? RR : 1)>, rows_bytes);    \
     }
+    PREP_ONE(1) PREP_ONE(2) PREP_ONE(4) PREP_ONE(8) PREP_ONE(16) PREP_ONE(32) PREP_ONE(64)
+#undef PREP_ONE
+    return err;
+}
+
+template <typename T>
+bdc_status sweep_prepare(bdc_engine *e, PrecBuf<T> &b) {
+    const size_t big = (size_t)(sizeof(T) == 4 ? 32768 : 16384) * sizeof(T);
+    BDC_CUDA_TRY(prepare_all<T>(big, big));
     (void)e;
+    (void)b;
     return BDC_OK;
 }
 
@@ -470,12 +762,17 @@ bdc_status sweep_forward(bdc_engine *e, PrecBuf<T> &b, const T *p_src, int apply
     size_t sm1 = tile_bytes_cols<T>(s);
     T *p = const_cast<T *>(p_src);
     dim3 g1(s.nblk_cols, e->nd);
-    k_cols_fwd<T><<<g1, SW_THREADS, sm1, e->stream>>>(a, p, b.D, b.F1, b.q, b.L, apply_update, mode); e->launches++; stage_mark(e, "cols_fwd");
+    const int rc = r_of(((size_t)1 << s.n1) << s.lw);
+    SW_WITH_R(rmax_fwd<T>(), rc,
+              (k_cols_fwd<T, R><<<g1, SW_THREADS, sm1, e->stream>>>(a, p, b.D, b.F1, b.q, b.L, apply_update, mode)));
+    e->launches++; stage_mark(e, "cols_fwd");
     BDC_CUDA_TRY(cudaGetLastError());
     if (s.n2 > 0) {
         size_t sm2 = tile_bytes_rows<T>(s);
         dim3 g2((2u << s.n1) - 1u, e->nd);
-        k_rows_fwd<T><<<g2, SW_THREADS, sm2, e->stream>>>(a, p, b.F1, b.Tm, b.Ts); e->launches++; stage_mark(e, "rows_fwd");
+        const int rr = r_of((size_t)1 << s.n2);
+        SW_WITH_R(rmax_fwd<T>(), rr, (k_rows_fwd<T, R><<<g2, SW_THREADS, sm2, e->stream>>>(a, p, b.F1, b.Tm, b.Ts)));
+        e->launches++; stage_mark(e, "rows_fwd");
         BDC_CUDA_TRY(cudaGetLastError());
         int nb = (int)std::min<size_t>(((size_t)2 << e->n) / 256 + 1, 148 * 16);
         dim3 g3(nb, e->nd);
@@ -492,7 +789,9 @@ bdc_status sweep_adjoint(bdc_engine *e, PrecBuf<T> &b, const T *Lsrc, const T *o
     if (s.n2 > 0) {
         size_t sm2 = tile_bytes_rows<T>(s);
         dim3 g2((2u << s.n1) - 1u, e->nd);
-        k_rows_adj<T><<<g2, SW_THREADS, sm2, e->stream>>>(a, Lsrc, omega, b.Gb); e->launches++; stage_mark(e, "rows_adj");
+        const int rr = r_of((size_t)2 << s.n2);
+        SW_WITH_R(rmax_adj<T>(), rr, (k_rows_adj<T, R><<<g2, SW_THREADS, sm2, e->stream>>>(a, Lsrc, omega, b.Gb)));
+        e->launches++; stage_mark(e, "rows_adj");
         BDC_CUDA_TRY(cudaGetLastError());
     }
     EpiArgs ep{};
@@ -508,7 +807,10 @@ bdc_status sweep_adjoint(bdc_engine *e, PrecBuf<T> &b, const T *Lsrc, const T *o
     }
     size_t sm1 = tile_bytes_cols<T>(s);
     dim3 g1(s.nblk_cols, e->nd);
-    k_cols_adj<T><<<g1, SW_THREADS, sm1, e->stream>>>(a, ep, b.Gb, Lsrc, omega, mode); e->launches++; stage_mark(e, "cols_adj");
+    const int rc = r_of(((size_t)2 << s.n1) << s.lw);
+    SW_WITH_R(rmax_adj<T>(), rc,
+              (k_cols_adj<T, R><<<g1, SW_THREADS, sm1, e->stream>>>(a, ep, b.Gb, Lsrc, omega, mode)));
+    e->launches++; stage_mark(e, "cols_adj");
     BDC_CUDA_TRY(cudaGetLastError());
     return BDC_OK;
 }
@@ -589,10 +891,8 @@ extern "C" bdc_status bdc_output_marginal_static(int n, double d, const double *
             bdc_set_error(std::string("bdc_output_marginal_static: cudaGetSymbolAddress: ") + cudaGetErrorString(err));
             return BDC_ECUDA;
         }
-        const Sched smax = make_sched(STATIC_MAXN, 8, 0, 0);
-        size_t cols = std::max(tile_bytes_cols<double>(smax), tile_bytes_cols<double>(make_sched(13, 8, 0, 0)));
-        BDC_CUDA_TRY(allow_smem(k_cols_fwd<double>, std::max(cols, tile_bytes_cols<double>(s))));
-        BDC_CUDA_TRY(allow_smem(k_rows_fwd<double>, tile_bytes_rows<double>(smax)));
+        const size_t big = (size_t)16384 * sizeof(double);
+        BDC_CUDA_TRY(prepare_all<double>(big, big));
         g_static_dev[dev].base = (double *)ptr;
     }
     double *base = g_static_dev[dev].base;
@@ -624,11 +924,15 @@ extern "C" bdc_status bdc_output_marginal_static(int n, double d, const double *
     a.inv_binom = wk;  // the combine's per-length weight: d^(n-k)(1-d)^k gives q(y) = sum_x p W
     k_static_init<<<1, 64, 0, st>>>(n, d, inst, wk, q_dev);
     double *p = const_cast<double *>(p_dev);  // read only: no update is applied
-    k_cols_fwd<double><<<dim3(s.nblk_cols, 1), SW_THREADS, tile_bytes_cols<double>(s), st>>>(
-        a, p, p, F1, q_dev, L, 0, MODE_DUAL);
+    const int rc = r_of(((size_t)1 << s.n1) << s.lw);
+    SW_WITH_R(rmax_fwd<double>(), rc,
+              (k_cols_fwd<double, R><<<dim3(s.nblk_cols, 1), SW_THREADS, tile_bytes_cols<double>(s), st>>>(
+                  a, p, p, F1, q_dev, L, 0, MODE_DUAL)));
     if (s.n2 > 0) {
-        k_rows_fwd<double><<<dim3((2u << s.n1) - 1u, 1), SW_THREADS, tile_bytes_rows<double>(s), st>>>(a, p, F1, Tm,
-                                                                                                     Ts);
+        const int rr = r_of((size_t)1 << s.n2);
+        SW_WITH_R(rmax_fwd<double>(), rr,
+                  (k_rows_fwd<double, R><<<dim3((2u << s.n1) - 1u, 1), SW_THREADS, tile_bytes_rows<double>(s), st>>>(
+                      a, p, F1, Tm, Ts)));
         int nb = (int)std::min<size_t>((2 * N) / 256 + 1, 148 * 16);
         k_combine<double><<<dim3(nb, 1), 256, 0, st>>>(a, p, F1, Tm, Ts, q_dev, L, MODE_DUAL);
     }
