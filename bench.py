@@ -199,20 +199,23 @@ def run_ours(args, rank: int, world: int):
     import torch.distributed as dist
 
     import paper_2604_05867_b300 as bdc
+    from paper_2604_05867_b300 import shard
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
-    n, d = N_BITS, D_VALUE
+    n = N_BITS
+    # weak scaling: one n = 24 instance per rank (the instances are independent)
+    (d,) = shard.shard([D_VALUE] * world, rank, world)
 
     with torch.cuda.stream(stream):
         t0 = time.perf_counter()
         eng = bdc.Engine(n, [d], options=bdc.default_options(enable_literal=1, chunk=8), stream=stream)
         a0_s = time.perf_counter() - t0
         # pick the sweep schedules for this GPU (part of the setup, not of a step)
-        sched32 = eng.autotune("fp32", reps=3)
-        sched64 = eng.autotune("fp64", reps=2)
+        sched32 = eng.autotune("fp32", reps=3, cache=args.sched_cache)
+        sched64 = eng.autotune("fp64", reps=2, cache=args.sched_cache)
 
         # warm-up: W untimed FP32 iterations
         eng.iterate(args.warmup, -1.0, "fp32", "sweep")
@@ -239,11 +242,8 @@ def run_ours(args, rank: int, world: int):
         ms_total = ev0.elapsed_time(ev1)
         launches = eng.launch_count() - launches0
         clk = clocks.stop()
-        ms = ms_total / args.steps
-        if world > 1:
-            t = torch.tensor([ms], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = shard.max_over_ranks(ms_total / args.steps, device=dev)  # slowest rank's time per step
+        # every rank iterates its own instance: the job covers `world` instances per step
         value = pairs_per_iteration(n) * world / (ms / 1000.0)
 
         extra = {}
@@ -339,6 +339,144 @@ def run_ours(args, rank: int, world: int):
         print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------
+# the configurations of the workload, each run end to end (one JSON line each)
+# ----------------------------------------------------------------------------
+def _sync_time(fn, stream):
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = fn()
+    torch.cuda.synchronize()
+    return out, time.perf_counter() - t0
+
+
+def run_config(args):
+    import torch
+
+    import paper_2604_05867_b300 as bdc
+    from paper_2604_05867_b300 import dual, inputs
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    res = {"config_run": args.config}
+    with torch.cuda.stream(stream):
+        if args.config == "ba10":
+            # plain FP64 BA at n=10, d=0.5: gap < 1e-9 or 2000 iterations; against the
+            # oracle's BA on the channel built from all 2^10 deletion patterns
+            import oracle
+            n, d, T, tol = 10, 0.5, 2000, 1e-9
+            t0 = time.perf_counter()
+            ref = oracle.ba_bdc(n, d, T, tol=tol)
+            t_or = time.perf_counter() - t0
+            for impl in ("sweep", "literal"):
+                eng = bdc.Engine(n, [d], stream=stream)
+                (lo, up, it), t = _sync_time(lambda: eng.iterate(T, tol, "fp64", impl), stream)
+                hlo, hup = eng.history(0)
+                m = min(len(hlo), len(ref["lower"]))
+                c = eng.certify()
+                res["gpu_" + impl] = {"iters": int(it[0]), "lower": float(lo[0]), "upper": float(up[0]),
+                                      "ms_per_iter": 1000 * t / max(1, it[0]),
+                                      "max_abs_diff_lower_vs_oracle": float(np.max(np.abs(hlo[:m] - ref["lower"][:m]))),
+                                      "max_abs_diff_upper_vs_oracle": float(np.max(np.abs(hup[:m] - ref["upper"][:m]))),
+                                      "certified_upper": float(c["upper"][0]), "margin": float(c["margin"][0])}
+                eng.close()
+            res["oracle"] = {"iters": int(ref["iters"]), "lower": float(ref["lower"][-1]),
+                             "upper": float(ref["upper"][-1]), "ms_per_iter": 1000 * t_or / ref["iters"]}
+        elif args.config == "n20":
+            # n=20, d=0.7: 500 FP32 iterations, FP64 certificate of C_20/20
+            import oracle
+            n, d, T = 20, 0.7, 500
+            eng = bdc.Engine(n, [d], options=bdc.default_options(enable_literal=0), stream=stream)
+            eng.autotune("fp32")
+            (lo, up, it), t = _sync_time(lambda: eng.iterate(T, -1.0, "fp32", "sweep"), stream)
+            c, tc = _sync_time(lambda: eng.certify(), stream)
+            res.update({"n": n, "d": d, "iters": T, "ms_per_iter": 1000 * t / T, "lower": float(lo[0]),
+                        "upper": float(up[0]), "certified_upper": float(c["upper"][0]),
+                        "certified_upper_over_n": float(c["upper"][0]) / n, "margin": float(c["margin"][0]),
+                        "certify_ms": 1000 * tc, "pairs_per_s_effective": pairs_per_iteration(n) * T / t})
+            if args.oracle_check:
+                p = eng.get_p()[0]
+                eps = 2.0 ** -30
+                t0 = time.perf_counter()
+                q = oracle.q_full(n, d, (1 - eps) * p + eps / (1 << n))
+                U, _ = oracle.certify(n, d, q)
+                res["oracle_certify"] = {"U": U, "diff": float(c["upper"][0]) - U, "seconds": time.perf_counter() - t0}
+            eng.close()
+        elif args.config == "batched":
+            # n=22 with 32 d in [0.05, 0.95] and n in {14,16,18,20} with 8 d each, one graph
+            grid = inputs.batched_d_grid()
+            T = args.iters or 500
+            opts = bdc.default_options(enable_literal=0, chunk=10)
+            engs = [bdc.Engine(n, ds, options=opts, stream=stream) for n, ds in grid.items()]
+            for e in engs:
+                e.autotune("fp32")
+            batch = bdc.Batch(engs, chunk=10)
+            batch.iterate(10, -1.0, "fp32")
+            ran, t = _sync_time(lambda: batch.iterate(T, -1.0, "fp32"), stream)
+            pairs = sum(pairs_per_iteration(e.n) * e.nd for e in engs)
+            certs, tc = _sync_time(lambda: [e.certify() for e in engs], stream)
+            res.update({"instances": sum(e.nd for e in engs), "iters": ran, "seconds": t,
+                        "ms_per_iter_all_instances": 1000 * t / ran,
+                        "pairs_per_s_effective": pairs * ran / t, "certify_seconds_all": tc,
+                        "certified_upper_over_n": {str(e.n): [round(float(u) / e.n, 8) for u in c["upper"]]
+                                                   for e, c in zip(engs, certs)},
+                        "max_margin": max(float(np.max(c["margin"])) for c in certs)})
+            batch.close()
+            for e in engs:
+                e.close()
+        elif args.config == "dual":
+            # n=22, d=0.8: 50 BA iterations -> theta; tau=1e-3; FD (h=1e-6, FP64) on 64
+            # random coordinates; 200 Adam steps; FP64 certified max_x D_x
+            n, d, tau, h = 22, 0.8, 1e-3, 1e-6
+            eng = bdc.Engine(n, [d], options=bdc.default_options(enable_literal=0), stream=stream)
+            eng.iterate(50, -1.0, "fp32", "sweep")
+            theta0 = dual.theta_from_q(eng, eng.get_q("fp64")[0])
+            th = torch.tensor(theta0, dtype=torch.float64, device="cuda")
+            (F, mD, g, gd), tg = _sync_time(lambda: eng.dual_bound(0, th, tau, "fp64", grad=True), stream)
+            g = g.cpu().numpy()
+            errs = []
+            for i in inputs.fd_coordinates(len(theta0), 64, seed=0):
+                tp, tm = th.clone(), th.clone()
+                tp[i] += h
+                tm[i] -= h
+                fd = (eng.dual_bound(0, tp, tau, "fp64", grad=False)[0] -
+                      eng.dual_bound(0, tm, tau, "fp64", grad=False)[0]) / (2 * h)
+                errs.append(abs(fd - g[i]) / max(1e-12, abs(g[i]), abs(fd)))
+            out, t = _sync_time(lambda: dual.optimize_dual(eng, 0, tau=tau, steps=200, lr=1e-2, ba_iters=0,
+                                                           precision="fp32", theta0=theta0), stream)
+            res.update({"n": n, "d": d, "tau": tau, "F": F, "max_D": mD, "dF_dd": gd,
+                        "value_and_grad_ms_fp64": 1000 * tg, "fd_coords": len(errs),
+                        "fd_max_rel_err": float(np.max(errs)), "fd_median_rel_err": float(np.median(errs)),
+                        "adam_steps": 200, "adam_seconds": t,
+                        "certified_initial": out["certified_initial"], "certified_final": out["certified_final"],
+                        "certified_final_over_n": out["certified_final"] / n, "margin": out["margin"]})
+            eng.close()
+        elif args.config == "large":
+            # n=26, 7 values of d, 300 FP32 iterations each, FP64 certificate of C_26(d)/(26(1-d))
+            from paper_2604_05867_b300.inputs import LARGE_SWEEP_D
+            n, T = 26, args.iters or 300
+            ds = LARGE_SWEEP_D
+            t0 = time.perf_counter()
+            eng = bdc.Engine(n, ds, options=bdc.default_options(enable_literal=0), stream=stream)
+            t_bind = time.perf_counter() - t0
+            eng.autotune("fp32")
+            (lo, up, it), t = _sync_time(lambda: eng.iterate(T, -1.0, "fp32", "sweep"), stream)
+            c, tc = _sync_time(lambda: eng.certify(), stream)
+            res.update({"n": n, "d": ds, "iters": T, "bind_precompute_s": t_bind, "seconds": t,
+                        "ms_per_iter_all_instances": 1000 * t / T,
+                        "pairs_per_s_effective": pairs_per_iteration(n) * len(ds) * T / t,
+                        "certify_seconds": tc, "workspace_gb": eng.ws_bytes / 1e9,
+                        "certified_upper": [float(u) for u in c["upper"]],
+                        "certified_over_n_1_minus_d": [float(u) / (n * (1 - dv)) for u, dv in zip(c["upper"], ds)],
+                        "margin_max": float(np.max(c["margin"])),
+                        "lower_last": [float(v) for v in lo], "upper_last": [float(v) for v in up]})
+            eng.close()
+        else:
+            raise SystemExit("unknown config " + args.config)
+    print(json.dumps(res), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -348,7 +486,16 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-literal", action="store_true")
+    ap.add_argument("--config", default=None, choices=["ba10", "n20", "batched", "dual", "large"],
+                    help="run one workload configuration end to end instead of the headline bench")
+    ap.add_argument("--iters", type=int, default=0)
+    ap.add_argument("--sched-cache", default=None,
+                    help="JSON file of tuned sweep schedules (read if present, written after a search)")
+    ap.add_argument("--oracle-check", action="store_true")
     args = ap.parse_args()
+    if args.config:
+        run_config(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     world = int(os.environ.get("WORLD_SIZE", "1"))

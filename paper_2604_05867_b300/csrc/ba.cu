@@ -115,18 +115,20 @@ __global__ void k_symmetrize(int n, T *D, const double *inst) {
         if (!seen) mids[nt++] = cand[t];
     }
     T *Dz = D + ((size_t)z << n);
+    // tile rows padded to H+1 elements: the reversed reads hit distinct banks
+    const uint32_t HP = H + 1u, TSP = H * HP, lg = 2 * hb;
     for (uint32_t e = threadIdx.x; e < nt * TS; e += blockDim.x) {
-        uint32_t t = e / TS, r = e % TS;
+        uint32_t t = e >> lg, r = e & (TS - 1u);
         uint32_t h = r >> hb, l = r & (H - 1u);
         size_t x = ((size_t)h << (n - hb)) | ((size_t)mids[t] << hb) | l;
-        tile[e] = Dz[x];
+        tile[t * TSP + h * HP + l] = Dz[x];
     }
     __syncthreads();
     // every element: the mean over its orbit, summed in the order of the
     // orbit representative's members, so all members get the same bits
     const uint32_t full = (1u << n) - 1u;
     for (uint32_t e = threadIdx.x; e < nt * TS; e += blockDim.x) {
-        uint32_t t = e / TS, r = e % TS;
+        uint32_t t = e >> lg, r = e & (TS - 1u);
         uint32_t h = r >> hb, l = r & (H - 1u);
         uint32_t x = (h << (n - hb)) | (mids[t] << hb) | l;
         uint32_t rp = orbit_rep_dev(x, n, nullptr);
@@ -139,7 +141,7 @@ __global__ void k_symmetrize(int n, T *D, const double *inst) {
             int ti = 0;
             for (int q = 0; q < nt; q++)
                 if (mids[q] == ym) ti = q;
-            v[s] = tile[ti * TS + ((y >> (n - hb)) << hb) + (y & (H - 1u))];
+            v[s] = tile[ti * TSP + (y >> (n - hb)) * HP + (y & (H - 1u))];
         }
         Dz[x] = ((v[0] + v[1]) + (v[2] + v[3])) * (T)0.25;
     }
@@ -315,7 +317,7 @@ template <typename T>
 bdc_status launch_symmetrize(bdc_engine *e, T *D) {
     const int n = e->n;
     const int hb = std::min(5, n / 2), nm = n - 2 * hb;
-    size_t smem = (size_t)4 * ((size_t)1 << (2 * hb)) * sizeof(T);
+    size_t smem = (size_t)4 * ((size_t)1 << hb) * (((size_t)1 << hb) + 1) * sizeof(T);
     dim3 g(1u << nm, e->nd);
     k_symmetrize<T><<<g, 256, smem, e->stream>>>(n, D, e->inst); e->launches++;
     k_clear_symneed<<<(e->nd + 63) / 64, 64, 0, e->stream>>>(e->nd, e->inst); e->launches++; stage_mark(e, "symmetrize");

@@ -124,7 +124,7 @@ struct bdc_engine {
     uint32_t *scan_tmp = nullptr; // block counts for compaction
     double *bk = nullptr;       // [nd][n+1] b_k (FP64, host-exact)
     double *tab_clog = nullptr; // [8192]: c*log2(c) and log2(c) for c < 4096 (literal path)
-    long long *tab_fix = nullptr; // [65536] round(c*log2(c)*2^34)
+    longlong2 *tab_fix = nullptr; // [65536] c*log2(c) = x + y * 2^-62 (x integer part)
     double *inst = nullptr;     // [nd][INST_STRIDE]
     double *hist = nullptr;     // [nd][2][BDC_HIST]
     double *lit_part = nullptr; // literal path partial buffer
@@ -196,7 +196,7 @@ int64_t literal_items(int n);
 size_t literal_part_bytes(int n, int nd);
 bdc_status upload_literal_tables(bdc_engine *e);
 bdc_status subseq_counts_impl(int n, const uint64_t *x_dev, int64_t nx, uint64_t *N_dev, double *S_dev,
-                              uint64_t *emb_dev, cudaStream_t st, const long long *tab_fix);
+                              uint64_t *emb_dev, cudaStream_t st, const longlong2 *tab_fix);
 
 // record a stage boundary when profiling (no-op otherwise)
 inline void stage_mark(bdc_engine *e, const char *name) {

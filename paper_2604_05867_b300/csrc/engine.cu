@@ -205,7 +205,7 @@ size_t carve(bdc_engine *e, char *base) {
     e->scan_tmp = c.take<uint32_t>(M / 2048 + 16);
     e->bk = c.take<double>((size_t)6 * nd * (n + 1));
     e->tab_clog = c.take<double>(8192);
-    e->tab_fix = c.take<long long>(65536);
+    e->tab_fix = c.take<longlong2>(65536);
     e->inst = c.take<double>((size_t)nd * INST_STRIDE);
     e->hist = c.take<double>((size_t)nd * 2 * BDC_HIST);
     e->pcert = c.take<double>(nd * N);
@@ -339,13 +339,14 @@ extern "C" bdc_status bdc_bind(bdc_engine *e, void *ws, size_t bytes, void *stre
         double *I = &inst[(size_t)z * INST_STRIDE];
         I[I_ACTIVE] = 1.0;
         I[I_TOL] = -1.0;
-        // certified bound on |Hb^ - Hb|: S_k is an exact int64 sum of terms each
-        // within 1.125 * 2^-35 (+4u relative for counts >= 65536) of
+        // certified bound on |Hb^ - Hb|: S_k is an exact integer sum of terms
+        // each within 2^-43 (long double table, |term| < 2^20, plus the 2^-62
+        // fraction rounding) or 4u relative + 2^-62 (counts >= 65536, FP64) of
         // count*log2(count), converted with one rounding; with N_k <= C(n,k)
-        // and S_k/C(n,k) <= log2 C(n,k): |H^_k - H_k| <= 2^-34 + 9u log2 C(n,k),
+        // and S_k/C(n,k) <= log2 C(n,k): |H^_k - H_k| <= 2^-43 + 9u log2 C(n,k),
         // then the products and the (n+1)-term sum:
-        // 1.05 (2^-34 + gamma_{n+14} sum_k b_k log2 C(n,k))
-        I[I_EH] = 1.05 * (std::ldexp(1.0, -34) + gamma_u((double)n + 14) * sum_blc);
+        // 1.05 (2^-43 + gamma_{n+14} sum_k b_k log2 C(n,k))
+        I[I_EH] = 1.05 * (std::ldexp(1.0, -43) + gamma_u((double)n + 14) * sum_blc);
         I[I_NEGH] = (double)negh;
         I[I_DUAL_C0] = (double)c0;
     }
@@ -354,8 +355,16 @@ extern "C" bdc_status bdc_bind(bdc_engine *e, void *ws, size_t bytes, void *stre
         tab[c] = (double)((long double)c * log2l((long double)c));
         tab[4096 + c] = (double)log2l((long double)c);
     }
-    std::vector<long long> tabfix(65536, 0);
-    for (int c = 2; c < 65536; c++) tabfix[c] = llrintl((long double)c * log2l((long double)c) * 17179869184.0L);
+    std::vector<longlong2> tabfix(65536);
+    for (int c = 0; c < 65536; c++) {
+        long double t = c < 2 ? 0.0L : (long double)c * log2l((long double)c);
+        long double ip = floorl(t);
+        unsigned long long f = (unsigned long long)llrintl((t - ip) * 4611686018427387904.0L);  // 2^62
+        long long i = (long long)ip;
+        if (f >= (1ull << 62)) { f -= (1ull << 62); i += 1; }
+        tabfix[c].x = i;
+        tabfix[c].y = (long long)f;
+    }
     BDC_CUDA_TRY(cudaMemcpyAsync(e->bk, bk.data(), bk.size() * sizeof(double), cudaMemcpyHostToDevice, e->stream));
     BDC_CUDA_TRY(cudaMemcpyAsync(e->dual_w, rb.data(), rb.size() * sizeof(double), cudaMemcpyHostToDevice,
                                  e->stream));
@@ -363,7 +372,7 @@ extern "C" bdc_status bdc_bind(bdc_engine *e, void *ws, size_t bytes, void *stre
                                  e->stream));
     BDC_CUDA_TRY(cudaMemcpyAsync(e->tab_clog, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice,
                                  e->stream));
-    BDC_CUDA_TRY(cudaMemcpyAsync(e->tab_fix, tabfix.data(), tabfix.size() * sizeof(long long),
+    BDC_CUDA_TRY(cudaMemcpyAsync(e->tab_fix, tabfix.data(), tabfix.size() * sizeof(longlong2),
                                  cudaMemcpyHostToDevice, e->stream));
     BDC_CUDA_TRY(cudaMemcpyAsync(e->inst, inst.data(), inst.size() * sizeof(double), cudaMemcpyHostToDevice,
                                  e->stream));

@@ -32,15 +32,33 @@ __device__ __forceinline__ uint32_t warp_excl_scan(uint32_t v, int lane) {
     return s - v;
 }
 
-// c*log2(c) in fixed point with 34 fractional bits: sum_{|y|=k} Count log2 Count
-// <= C(n,k) log2 C(n,k) < 2^29 for n <= 26, so an int64 sum never overflows and
-// the accumulation needs no floating point (FP64 issue is scarce on B300).
-// Table entries (c < 65536) are host-rounded from long double; larger counts
-// are rounded from FP64 here.
-constexpr double FIX_SCALE = 17179869184.0;  // 2^34
-__device__ __forceinline__ long long clog2c_fix(uint32_t c, const long long *__restrict__ tab) {
-    if (tab != nullptr && c < 65536u) return __ldg(tab + c);
-    return c <= 1u ? 0ll : llrint((double)c * log2((double)c) * FIX_SCALE);
+// c*log2(c) as an integer part and a 62-bit fraction, summed exactly in two
+// 64-bit integers (the fraction carries into the integer part), so the hot
+// loop uses no floating point (FP64 issue is scarce on B300).  Table entries
+// (c < 65536) come from long double on the host; larger counts are split
+// from FP64 here.  sum_{|y|=k} Count log2 Count <= C(n,k) log2 C(n,k) < 2^28.
+constexpr double FRAC_SCALE = 4611686018427387904.0;  // 2^62
+constexpr unsigned long long FRAC_ONE = 1ull << 62;
+__device__ __forceinline__ void clog2c_fix(uint32_t c, const longlong2 *__restrict__ tab, long long &accI,
+                                           unsigned long long &accF) {
+    long long I;
+    unsigned long long F;
+    if (tab != nullptr && c < 65536u) {
+        longlong2 t = __ldg(tab + c);
+        I = t.x;
+        F = (unsigned long long)t.y;
+    } else if (c <= 1u) {
+        return;
+    } else {
+        double t = (double)c * log2((double)c);
+        double fi = floor(t);
+        I = (long long)fi;
+        F = __double2ull_rn((t - fi) * FRAC_SCALE);
+        if (F >= FRAC_ONE) { F -= FRAC_ONE; I += 1; }
+    }
+    accI += I;
+    accF += F;  // both < 2^62 before the add: no overflow
+    if (accF >= FRAC_ONE) { accF -= FRAC_ONE; accI += 1; }
 }
 
 // ---------------------------------------------------------------------------
@@ -165,7 +183,7 @@ struct WalkArgs {
     uint32_t *counter;          // dynamic work counter (may be null: static)
     // WALK_STATS
     uint32_t *Nk32; uint64_t *Nk64; double *Sk; int stride;
-    const long long *tabfix;    // c*log2(c)*2^34 for c < 65536
+    const longlong2 *tabfix;    // c*log2(c) split as (integer, fraction * 2^62) for c < 65536
     const double *tab_log2;     // log2(c) for c < 4096
     // WALK_LITERAL_D
     const double *L;            // [nd][2^(n+1)] log2 q_k
@@ -208,7 +226,8 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
         // per-lane accumulators: lane k owns length k (stats) / a 32-slot
         // gather buffer (literal D)
         uint32_t accN = (lane == 0) ? 1u : 0u;
-        long long accS = 0;
+        long long accI = 0;
+        unsigned long long accF = 0;
         double accD = 0.0;
         uint32_t bcode = 0, bcnt = 0;
         int nbuf = 0;
@@ -239,7 +258,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
             int k = bitlen32(code) - 1;
             // record (code, k, cnt)
             if (MODE == WALK_STATS) {
-                if (lane == k) { accN++; accS += clog2c_fix(cnt, a.tabfix); }
+                if (lane == k) { accN++; clog2c_fix(cnt, a.tabfix, accI, accF); }
             } else if (MODE == WALK_EMIT) {
                 if (lane == 0) a.emb[code] = cnt;
             } else {
@@ -272,7 +291,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
             if (lane <= n) {
                 if (a.Nk32) a.Nk32[item * a.stride + lane] = accN;
                 if (a.Nk64) a.Nk64[item * a.stride + lane] = accN;
-                if (a.Sk) a.Sk[item * a.stride + lane] = (double)accS * (1.0 / FIX_SCALE);
+                if (a.Sk) a.Sk[item * a.stride + lane] = (double)accI + (double)accF * (1.0 / FRAC_SCALE);
             }
         } else if (MODE == WALK_LITERAL_D) {
             if (lane < nbuf) {
@@ -591,7 +610,7 @@ bdc_status launch_literal_q(bdc_engine *e) {
 // test hook
 // ---------------------------------------------------------------------------
 bdc_status subseq_counts_impl(int n, const uint64_t *x_dev, int64_t nx, uint64_t *N_dev, double *S_dev,
-                              uint64_t *emb_dev, cudaStream_t st, const long long *tab_fix) {
+                              uint64_t *emb_dev, cudaStream_t st, const longlong2 *tab_fix) {
     WalkArgs a{};
     a.n = n;
     a.count = nx;

@@ -418,17 +418,38 @@ __global__ void __launch_bounds__(SW_THREADS) k_cols_fwd(SweepArgs a, T *p, cons
     const T shift = (T)inst[I_SHIFT];
     const uint32_t ntop = (1u << n1) << lw;
     T psum = (T)0;  // per-thread partial in the working precision, block sum in FP64
-    for (uint32_t e = threadIdx.x; e < ntop; e += SW_THREADS) {
-        uint32_t x1 = e >> lw, c = e & (w - 1u);
-        size_t x = ((size_t)x1 << n2) | (col0 + c);
-        T v = pz[x];
-        if (upd) {
-            v = v * exp2_t<T>(Dz[x] - shift);
-            pz[x] = v;
+    if (lw >= 2) {
+        // 4 consecutive columns of one row per step: 16-byte global accesses
+#pragma unroll 4
+        for (uint32_t e = 4 * threadIdx.x; e < ntop; e += 4 * SW_THREADS) {
+            uint32_t x1 = e >> lw, c = e & (w - 1u);
+            size_t x = ((size_t)x1 << n2) | (col0 + c);
+            T v[4], dv[4];
+            ld4(pz + x, v);
+            if (upd) {
+                ld4(Dz + x, dv);
+#pragma unroll
+                for (int k = 0; k < 4; k++) v[k] = v[k] * exp2_t<T>(dv[k] - shift);
+                st4(pz + x, v);
+            }
+            st4(buf + ntop + e, v);
+            T zero[4] = {(T)0, (T)0, (T)0, (T)0};
+            st4(buf + e, zero);
+            psum += (v[0] + v[1]) + (v[2] + v[3]);
         }
-        buf[ntop + e] = v;
-        buf[e] = (T)0;
-        psum += v;
+    } else {
+        for (uint32_t e = threadIdx.x; e < ntop; e += SW_THREADS) {
+            uint32_t x1 = e >> lw, c = e & (w - 1u);
+            size_t x = ((size_t)x1 << n2) | (col0 + c);
+            T v = pz[x];
+            if (upd) {
+                v = v * exp2_t<T>(Dz[x] - shift);
+                pz[x] = v;
+            }
+            buf[ntop + e] = v;
+            buf[e] = (T)0;
+            psum += v;
+        }
     }
     double s = block_sum<T>((double)psum, red);
     if (threadIdx.x == 0 && (mode == MODE_ITER || mode == MODE_DIV)) {
@@ -439,9 +460,19 @@ __global__ void __launch_bounds__(SW_THREADS) k_cols_fwd(SweepArgs a, T *p, cons
     lsweep_fwd_any<T, R>(buf, n1, lw);
     if (n2 > 0) {
         T *Fz = F1 + z * a.strideN;
-        for (uint32_t e = threadIdx.x + w; e < ntop; e += SW_THREADS) {
-            uint32_t row = e >> lw, c = e & (w - 1u);
-            Fz[((size_t)row << n2) | (col0 + c)] = buf[e];
+        if (lw >= 2) {
+#pragma unroll 4
+            for (uint32_t e = w + 4 * threadIdx.x; e < ntop; e += 4 * SW_THREADS) {
+                uint32_t row = e >> lw, c = e & (w - 1u);
+                T v[4];
+                ld4(buf + e, v);
+                st4(Fz + (((size_t)row << n2) | (col0 + c)), v);
+            }
+        } else {
+            for (uint32_t e = threadIdx.x + w; e < ntop; e += SW_THREADS) {
+                uint32_t row = e >> lw, c = e & (w - 1u);
+                Fz[((size_t)row << n2) | (col0 + c)] = buf[e];
+            }
         }
     } else {
         T *qz = q + z * a.strideM, *Lz = L + z * a.strideM;
@@ -570,9 +601,19 @@ __global__ void __launch_bounds__(SW_THREADS) k_cols_adj(SweepArgs a, EpiArgs ep
     const uint32_t nall = (2u << n1) << lw;
     if (n2 > 0) {
         const T *Gz = Gb + z * a.strideM;
-        for (uint32_t e = threadIdx.x; e < nall; e += SW_THREADS) {
-            uint32_t row = e >> lw, c = e & (w - 1u);
-            buf[e] = row ? Gz[((size_t)row << n2) | (col0 + c)] : (T)0;
+        if (lw >= 2) {
+#pragma unroll 4
+            for (uint32_t e = 4 * threadIdx.x; e < nall; e += 4 * SW_THREADS) {
+                uint32_t row = e >> lw, c = e & (w - 1u);
+                T v[4] = {(T)0, (T)0, (T)0, (T)0};
+                if (row) ld4(Gz + (((size_t)row << n2) | (col0 + c)), v);
+                st4(buf + e, v);
+            }
+        } else {
+            for (uint32_t e = threadIdx.x; e < nall; e += SW_THREADS) {
+                uint32_t row = e >> lw, c = e & (w - 1u);
+                buf[e] = row ? Gz[((size_t)row << n2) | (col0 + c)] : (T)0;
+            }
         }
     } else {
         const T *Lz = Lsrc + z * a.strideM;
@@ -588,7 +629,26 @@ __global__ void __launch_bounds__(SW_THREADS) k_cols_adj(SweepArgs a, EpiArgs ep
     double sZ = 0.0, mD = -INFINITY, sP = 0.0, mP = -INFINITY;
     T tZ = (T)0, tM = (T)-INFINITY;  // MODE_ITER partials in the working precision
     const double add = (mode == MODE_DIV) ? inst[I_SUMP] : 0.0;
-    for (uint32_t e = threadIdx.x; e < ntop; e += SW_THREADS) {
+    if (mode == MODE_ITER && lw >= 2) {
+        T *Dz = reinterpret_cast<T *>(ep.Dout) + z * a.strideN;
+#pragma unroll 2
+        for (uint32_t e = 4 * threadIdx.x; e < ntop; e += 4 * SW_THREADS) {
+            uint32_t x1 = e >> lw, c = e & (w - 1u);
+            size_t x = ((size_t)x1 << n2) | (col0 + c);
+            T G[4], hb[4], pv[4], Dv[4];
+            ld4(buf + ntop + e, G);
+            ld4(Hbz + x, hb);
+            ld4(pz + x, pv);
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                Dv[k] = -hb[k] - G[k];
+                tZ += pv[k] * exp2_t<T>(Dv[k]);
+                tM = Dv[k] > tM ? Dv[k] : tM;
+            }
+            st4(Dz + x, Dv);
+        }
+    }
+    for (uint32_t e = threadIdx.x; e < ntop && !(mode == MODE_ITER && lw >= 2); e += SW_THREADS) {
         uint32_t x1 = e >> lw, c = e & (w - 1u);
         size_t x = ((size_t)x1 << n2) | (col0 + c);
         T G = buf[ntop + e];
@@ -716,6 +776,7 @@ Sched make_sched(int n, int elem_bytes, int n2_override, int w_override) {
     int n2max = 13;
     int n2 = n2_override ? n2_override : std::min(n - 1, n2max);
     if (n2 < 5) n2 = std::min(5, n - 1);
+    if (n - n2 > nsingle) n2 = n - nsingle;  // the columns tile must hold 2^(n1+1) rows
     s.n2 = n2;
     s.n1 = n - n2;
     int lw = 0;
