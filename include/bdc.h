@@ -72,6 +72,10 @@ typedef struct {
     int sched_n2_fp32, sched_w_fp32, sched_n2_fp64, sched_w_fp64;
     /* Reserve the buffers of the literal (enumeration) path.  Default 1. */
     int enable_literal;
+    /* While p is complement-invariant (true for BA iterates from a uniform
+     * start, Appendix A), compute only half of every sweep and mirror the
+     * rest.  Default 1. */
+    int use_half;
 } bdc_options;
 
 /* Fill *opt with the defaults above. */
@@ -156,7 +160,9 @@ bdc_status bdc_certify_upper(bdc_engine *eng, const double *q_dev, double *upper
 /* p of every instance, normalised, host [nd][2^n]. */
 bdc_status bdc_get_p(bdc_engine *eng, double *p_host);
 /* Set p of every instance from host [nd][2^n] (non-negative, positive sum;
- * normalised here).  Clears the bound history. */
+ * normalised here).  Clears the bound history.  A p that is not invariant
+ * under complement (and reversal) switches off the half-sweep mode (and the
+ * orbit mean of D, and the literal path, which then returns BDC_EINVAL). */
 bdc_status bdc_set_p(bdc_engine *eng, const double *p_host);
 /* Output marginal q of the current p, host [nd][2^(n+1)] by code, computed in
  * the given precision. */

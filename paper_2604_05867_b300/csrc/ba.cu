@@ -95,8 +95,10 @@ __global__ void k_finalize_sum(int nd, const double *part, int maxblk, int nblk,
 // cpl rev mid, so one CTA per representative mid loads those tiles, and the
 // thread owning the orbit representative writes one canonical mean to all
 // members (bit-identical across the orbit).
+// n2h > 0: complement half mode, only inputs whose bit (n2h-1) is 0 are
+// stored and written; the others are read as their complements
 template <typename T>
-__global__ void k_symmetrize(int n, T *D, const double *inst) {
+__global__ void k_symmetrize(int n, T *D, const double *inst, int n2h) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *tile = reinterpret_cast<T *>(smem_raw);
     const int z = blockIdx.y;
@@ -121,6 +123,7 @@ __global__ void k_symmetrize(int n, T *D, const double *inst) {
         uint32_t t = e >> lg, r = e & (TS - 1u);
         uint32_t h = r >> hb, l = r & (H - 1u);
         size_t x = ((size_t)h << (n - hb)) | ((size_t)mids[t] << hb) | l;
+        if (n2h && ((x >> (n2h - 1)) & 1u)) x ^= (size_t)((1u << n) - 1u);
         tile[t * TSP + h * HP + l] = Dz[x];
     }
     __syncthreads();
@@ -143,7 +146,19 @@ __global__ void k_symmetrize(int n, T *D, const double *inst) {
                 if (mids[q] == ym) ti = q;
             v[s] = tile[ti * TSP + (y >> (n - hb)) * HP + (y & (H - 1u))];
         }
+        if (n2h && ((x >> (n2h - 1)) & 1u)) continue;
         Dz[x] = ((v[0] + v[1]) + (v[2] + v[3])) * (T)0.25;
+    }
+}
+
+// complement half mode -> full arrays: a[x] = a[cpl x] where bit (n2-1) of x is 1
+template <typename T>
+__global__ void k_mirror_half(int n, int n2, int nd, T *a) {
+    const size_t N = (size_t)1 << n;
+    const uint32_t full = (1u << n) - 1u;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N * nd; i += (size_t)gridDim.x * blockDim.x) {
+        const uint32_t x = (uint32_t)(i & (N - 1));
+        if ((x >> (n2 - 1)) & 1u) a[i] = a[(i & ~(N - 1)) | (x ^ full)];
     }
 }
 
@@ -293,11 +308,11 @@ bdc_status launch_build_Hb_w(bdc_engine *e, const double *w, double *out) {
 }
 
 template <typename T>
-bdc_status launch_finalize(bdc_engine *e, PrecBuf<T> &b, int mode, int add_negh) {
+bdc_status launch_finalize(bdc_engine *e, PrecBuf<T> &b, int mode, int add_negh, int nblk) {
     int maxblk = part_maxblk(e);
+    if (nblk <= 0) nblk = b.s.nblk_cols;
     if (mode == MODE_ITER) {
-        k_finalize_iter<<<e->nd, FIN_THREADS, 0, e->stream>>>(e->nd, b.part, maxblk, b.s.nblk_cols, b.s.nblk_cols,
-                                                              e->inst, e->hist); e->launches++; stage_mark(e, "finalize");
+        k_finalize_iter<<<e->nd, FIN_THREADS, 0, e->stream>>>(e->nd, b.part, maxblk, nblk, nblk, e->inst, e->hist); e->launches++; stage_mark(e, "finalize");
     } else {
         k_finalize_sum<<<e->nd, FIN_THREADS, 0, e->stream>>>(e->nd, b.part, maxblk, b.s.nblk_cols, e->inst,
                                                              add_negh); e->launches++;
@@ -314,12 +329,19 @@ bdc_status launch_finalize_literal(bdc_engine *e, int nblk0, int nblk1) {
 }
 
 template <typename T>
-bdc_status launch_symmetrize(bdc_engine *e, T *D) {
+bdc_status launch_mirror_half(bdc_engine *e, T *a, int n2) {
+    k_mirror_half<T><<<grid_for((size_t)e->nd << e->n, 256), 256, 0, e->stream>>>(e->n, n2, e->nd, a); e->launches++;
+    BDC_CUDA_TRY(cudaGetLastError());
+    return BDC_OK;
+}
+
+template <typename T>
+bdc_status launch_symmetrize(bdc_engine *e, T *D, int n2h) {
     const int n = e->n;
     const int hb = std::min(5, n / 2), nm = n - 2 * hb;
     size_t smem = (size_t)4 * ((size_t)1 << hb) * (((size_t)1 << hb) + 1) * sizeof(T);
     dim3 g(1u << nm, e->nd);
-    k_symmetrize<T><<<g, 256, smem, e->stream>>>(n, D, e->inst); e->launches++;
+    k_symmetrize<T><<<g, 256, smem, e->stream>>>(n, D, e->inst, n2h); e->launches++;
     k_clear_symneed<<<(e->nd + 63) / 64, 64, 0, e->stream>>>(e->nd, e->inst); e->launches++; stage_mark(e, "symmetrize");
     BDC_CUDA_TRY(cudaGetLastError());
     return BDC_OK;
@@ -365,9 +387,11 @@ bdc_status launch_expand_reps(bdc_engine *e, const double *Dr, double *out) {
 
 template bdc_status launch_build_Hb<float>(bdc_engine *, PrecBuf<float> &);
 template bdc_status launch_build_Hb<double>(bdc_engine *, PrecBuf<double> &);
-template bdc_status launch_finalize<float>(bdc_engine *, PrecBuf<float> &, int, int);
-template bdc_status launch_finalize<double>(bdc_engine *, PrecBuf<double> &, int, int);
-template bdc_status launch_symmetrize<float>(bdc_engine *, float *);
-template bdc_status launch_symmetrize<double>(bdc_engine *, double *);
+template bdc_status launch_finalize<float>(bdc_engine *, PrecBuf<float> &, int, int, int);
+template bdc_status launch_finalize<double>(bdc_engine *, PrecBuf<double> &, int, int, int);
+template bdc_status launch_symmetrize<float>(bdc_engine *, float *, int);
+template bdc_status launch_symmetrize<double>(bdc_engine *, double *, int);
+template bdc_status launch_mirror_half<float>(bdc_engine *, float *, int);
+template bdc_status launch_mirror_half<double>(bdc_engine *, double *, int);
 template bdc_status launch_apply_pending<float>(bdc_engine *, PrecBuf<float> &);
 template bdc_status launch_apply_pending<double>(bdc_engine *, PrecBuf<double> &);

@@ -143,6 +143,10 @@ struct bdc_engine {
     // graph cache per (precision, impl)
     cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     int cur = 0;                // representation holding the current p: 0 FP32, 1 FP64, 2 literal
+    bool half_ok = true;        // p is complement-invariant (uniform start, BA iterates)
+    bool orbit_ok = true;       // p is invariant under complement and reversal
+    bool half_active[2] = {false, false};  // upper half of p/D stale in that precision
+    int half_n2[2] = {0, 0};    // n2 of the schedule the half mode ran with
     int64_t iters_total = 0;
     int64_t launches = 0;       // kernels launched so far (graph replays included)
     int64_t graph_kernels[2][2] = {{0, 0}, {0, 0}};
@@ -171,18 +175,22 @@ bdc_status launch_literal_D(bdc_engine *e);
 template <typename T>
 bdc_status sweep_prepare(bdc_engine *e, PrecBuf<T> &b);
 template <typename T>
-bdc_status sweep_forward(bdc_engine *e, PrecBuf<T> &b, const T *p_src, int apply_update, int mode);
+bdc_status sweep_forward(bdc_engine *e, PrecBuf<T> &b, const T *p_src, int apply_update, int mode, bool half = false);
 template <typename T>
-bdc_status sweep_adjoint(bdc_engine *e, PrecBuf<T> &b, const T *Lsrc, const T *omega, T *Dout, int mode);
+bdc_status sweep_adjoint(bdc_engine *e, PrecBuf<T> &b, const T *Lsrc, const T *omega, T *Dout, int mode,
+                         bool half = false);
+bool half_possible(const Sched &s);
 
 // BA glue (ba.cu)
 template <typename T>
 bdc_status launch_build_Hb(bdc_engine *e, PrecBuf<T> &b);
 bdc_status launch_build_Hb_w(bdc_engine *e, const double *w, double *out);
 template <typename T>
-bdc_status launch_finalize(bdc_engine *e, PrecBuf<T> &b, int mode, int add_negh = 0);
+bdc_status launch_finalize(bdc_engine *e, PrecBuf<T> &b, int mode, int add_negh = 0, int nblk = 0);
 template <typename T>
-bdc_status launch_symmetrize(bdc_engine *e, T *D);
+bdc_status launch_symmetrize(bdc_engine *e, T *D, int n2h = 0);
+template <typename T>
+bdc_status launch_mirror_half(bdc_engine *e, T *a, int n2);
 template <typename T>
 bdc_status launch_apply_pending(bdc_engine *e, PrecBuf<T> &b);
 bdc_status launch_literal_update(bdc_engine *e);

@@ -237,6 +237,7 @@ extern "C" void bdc_default_options(bdc_options *o) {
     o->q_floor = 1e-30;
     o->certify_mix = 9.313225746154785e-10;  // 2^-30
     o->enable_literal = 1;
+    o->use_half = 1;
 }
 
 extern "C" bdc_status bdc_create(int n, const double *d, int nd, const bdc_options *opt, bdc_engine **out) {
@@ -416,7 +417,32 @@ extern "C" bdc_status bdc_bind(bdc_engine *e, void *ws, size_t bytes, void *stre
 // ---------------------------------------------------------------------------
 // representations of p: 0 = FP32 sweep, 1 = FP64 sweep, 2 = literal (FP64)
 // ---------------------------------------------------------------------------
+// complement half mode left: rebuild the upper half of p and D
+static bdc_status unhalf(bdc_engine *e) {
+    if (e->half_active[0]) {
+        BDC_TRY(launch_mirror_half<float>(e, e->f32.p, e->half_n2[0]));
+        BDC_TRY(launch_mirror_half<float>(e, e->f32.D, e->half_n2[0]));
+        e->half_active[0] = false;
+    }
+    if (e->half_active[1]) {
+        BDC_TRY(launch_mirror_half<double>(e, e->f64.p, e->half_n2[1]));
+        BDC_TRY(launch_mirror_half<double>(e, e->f64.D, e->half_n2[1]));
+        e->half_active[1] = false;
+    }
+    return BDC_OK;
+}
+
+static void drop_graphs(bdc_engine *e) {
+    for (int a = 0; a < 2; a++)
+        for (int b = 0; b < 2; b++)
+            if (e->graph[a][b]) {
+                cudaGraphExecDestroy(e->graph[a][b]);
+                e->graph[a][b] = nullptr;
+            }
+}
+
 static bdc_status materialize(bdc_engine *e) {
+    BDC_TRY(unhalf(e));
     BDC_TRY(activate(e, -1.0));
     if (e->cur == 0) return launch_apply_pending<float>(e, e->f32);
     if (e->cur == 1) return launch_apply_pending<double>(e, e->f64);
@@ -450,11 +476,18 @@ static bdc_status make_current(bdc_engine *e, int target) {
 // iteration
 // ---------------------------------------------------------------------------
 template <typename T>
-static bdc_status iter_sweep(bdc_engine *e, PrecBuf<T> &b) {
-    BDC_TRY(sweep_forward<T>(e, b, b.p, 1, MODE_ITER));
-    BDC_TRY(sweep_adjoint<T>(e, b, b.L, b.omega, b.D, MODE_ITER));
-    BDC_TRY(launch_finalize<T>(e, b, MODE_ITER));
-    if (e->opt.symmetrize) BDC_TRY(launch_symmetrize<T>(e, b.D));
+static bdc_status iter_sweep(bdc_engine *e, PrecBuf<T> &b, int prec) {
+    // complement half mode while p is complement-invariant
+    const bool half = e->opt.use_half && e->half_ok && half_possible(b.s);
+    if (!half && e->half_active[prec]) BDC_TRY(unhalf(e));
+    BDC_TRY(sweep_forward<T>(e, b, b.p, 1, MODE_ITER, half));
+    BDC_TRY(sweep_adjoint<T>(e, b, b.L, b.omega, b.D, MODE_ITER, half));
+    BDC_TRY(launch_finalize<T>(e, b, MODE_ITER, 0, half ? b.s.nblk_cols / 2 : b.s.nblk_cols));
+    if (e->opt.symmetrize && e->orbit_ok) BDC_TRY(launch_symmetrize<T>(e, b.D, half ? b.s.n2 : 0));
+    if (half) {
+        e->half_active[prec] = true;
+        e->half_n2[prec] = b.s.n2;
+    }
     return BDC_OK;
 }
 
@@ -470,7 +503,7 @@ static bdc_status iter_literal(bdc_engine *e) {
 
 static bdc_status iter_once(bdc_engine *e, int prec, int impl) {
     if (impl == BDC_LITERAL) return iter_literal(e);
-    return prec == BDC_FP32 ? iter_sweep<float>(e, e->f32) : iter_sweep<double>(e, e->f64);
+    return prec == BDC_FP32 ? iter_sweep<float>(e, e->f32, 0) : iter_sweep<double>(e, e->f64, 1);
 }
 
 static bdc_status get_graph(bdc_engine *e, int prec, int impl, cudaGraphExec_t *out) {
@@ -504,6 +537,9 @@ extern "C" bdc_status bdc_ba_iterate(bdc_engine *e, int max_iters, double tol, i
     if (max_iters < 0 || (prec != BDC_FP32 && prec != BDC_FP64) || (impl != BDC_SWEEP && impl != BDC_LITERAL))
         BDC_FAIL(BDC_EINVAL, "bdc_ba_iterate: bad max_iters, precision or impl");
     if (impl == BDC_LITERAL && prec != BDC_FP64) BDC_FAIL(BDC_EINVAL, "bdc_ba_iterate: the literal path is FP64 only");
+    if (impl == BDC_LITERAL && !e->orbit_ok)
+        BDC_FAIL(BDC_EINVAL, "bdc_ba_iterate: the literal path works on orbit representatives and needs an "
+                             "orbit-invariant p (complement and reversal)");
     BDC_TRY(make_current(e, impl == BDC_LITERAL ? 2 : prec));
     BDC_TRY(activate(e, tol));
     const bool graph = e->opt.use_graph && e->stream != nullptr;
@@ -554,6 +590,7 @@ struct bdc_batch {
     cudaStream_t main = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int64_t graph_kernels[2] = {0, 0};
+    std::vector<int> half_state[2];  // engines' complement-half decisions baked into each graph
     int chunk = 8;
 };
 
@@ -600,6 +637,13 @@ extern "C" void bdc_batch_destroy(bdc_batch *b) {
 }
 
 static bdc_status batch_graph(bdc_batch *b, int prec, cudaGraphExec_t *out) {
+    std::vector<int> hs;
+    for (bdc_engine *e : b->engs) hs.push_back(e->half_ok ? 1 : 0);
+    if (b->graph[prec] && hs != b->half_state[prec]) {
+        cudaGraphExecDestroy(b->graph[prec]);
+        b->graph[prec] = nullptr;
+    }
+    b->half_state[prec] = hs;
     if (!b->graph[prec]) {
         cudaGraph_t graph;
         std::vector<int64_t> before(b->engs.size());
@@ -832,6 +876,24 @@ static bdc_status upload_p(bdc_engine *e, const double *p_host, bool normalize) 
         if (normalize)
             for (size_t x = 0; x < N; x++) p[z * N + x] /= s;
     }
+    // complement half mode needs p(x) == p(cpl x) exactly; the orbit mean of D
+    // and the literal path (work on orbit representatives) need invariance
+    // under reversal too
+    bool sym = true, orb = true;
+    const size_t full = N - 1;
+    const int n = e->n;
+    for (size_t i = 0; i < cnt && (sym || orb); i++) {
+        const size_t base = i & ~full, x = i & full;
+        size_t rx = 0;
+        for (int t = 0; t < n; t++) rx |= ((x >> t) & 1u) << (n - 1 - t);
+        sym = sym && p[i] == p[base | (x ^ full)];
+        orb = orb && p[i] == p[base | rx];
+    }
+    orb = orb && sym;
+    if (sym != e->half_ok || orb != e->orbit_ok) drop_graphs(e);
+    e->half_ok = sym;
+    e->orbit_ok = orb;
+    e->half_active[0] = e->half_active[1] = false;
     BDC_CUDA_TRY(cudaMemcpyAsync(e->f64.p, p.data(), cnt * sizeof(double), cudaMemcpyHostToDevice, e->stream));
     BDC_TRY(sync_check(e, "bdc_set_p upload"));
     const int g = grid_for(cnt, 256);

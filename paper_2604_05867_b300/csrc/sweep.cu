@@ -384,6 +384,22 @@ __device__ __forceinline__ double block_max(double v, double *red) {
     return s;
 }
 
+// Complement half mode (p(x) = p(cpl x)): every sweep quantity is invariant
+// under complementing all its strings, so only half of it is computed:
+//  - column chunks with x2 < 2^(n2-1); the other columns are the complements;
+//  - rows c1 in H1 = {empty} u {codes whose first symbol is 0}; row r of the
+//    half grid is c1 = 1 (r = 0) or r + 2^(bitlen(r)-1);
+//  - output codes in H1, written together with their complement.
+__device__ __forceinline__ uint32_t half_row(uint32_t r) { return r == 0 ? 1u : r + (1u << (bitlen32(r) - 1)); }
+__device__ __forceinline__ uint32_t cpl_code(uint32_t c) {
+    const int j = bitlen32(c) - 1;
+    return c ^ ((1u << j) - 1u);
+}
+__device__ __forceinline__ bool in_h1(uint32_t c) {
+    const int j = bitlen32(c) - 1;
+    return j == 0 || !((c >> (j - 1)) & 1u);
+}
+
 struct SweepArgs {
     int n, n1, n2, lw;
     int nblk;                 // column CTAs per instance
@@ -400,7 +416,7 @@ struct SweepArgs {
 // Prologue applies the pending BA update p <- p 2^{Dbar - shift} and writes
 // p back.  With n2 == 0 the pass covers all n symbols and writes q, L.
 // ---------------------------------------------------------------------------
-template <typename T, int R>
+template <typename T, int R, bool HALF>
 __global__ void __launch_bounds__(SW_THREADS) k_cols_fwd(SweepArgs a, T *p, const T *D, T *F1, T *q, T *L,
                                                           int apply_update, int mode) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -451,7 +467,8 @@ __global__ void __launch_bounds__(SW_THREADS) k_cols_fwd(SweepArgs a, T *p, cons
             psum += v;
         }
     }
-    double s = block_sum<T>((double)psum, red);
+    // in half mode each column x2 also stands for its complement column
+    double s = block_sum<T>((double)psum * (HALF ? 2.0 : 1.0), red);
     if (threadIdx.x == 0 && (mode == MODE_ITER || mode == MODE_DIV)) {
         double *pp = a.part + ((size_t)z * 2 + 0) * a.maxblk * 4 + blockIdx.x * 4;
         pp[0] = s;
@@ -487,20 +504,31 @@ __global__ void __launch_bounds__(SW_THREADS) k_cols_fwd(SweepArgs a, T *p, cons
 
 // pass 2 forward (rows): one row c1 per CTA; input row = F1[c1] (c1 < 2^n1)
 // or p[x1 = c1 - 2^n1]; output codes c2 < 32 go to the transposed Ts.
-template <typename T, int R>
+template <typename T, int R, bool HALF>
 __global__ void __launch_bounds__(SW_THREADS) k_rows_fwd(SweepArgs a, const T *p, const T *F1, T *Tm, T *Ts) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *buf = reinterpret_cast<T *>(smem_raw);
     const int z = blockIdx.y;
     if (a.inst[z * INST_STRIDE + I_ACTIVE] == 0.0) return;
     const int n1 = a.n1, n2 = a.n2;
-    const uint32_t c1 = blockIdx.x + 1;
+    const uint32_t c1 = HALF ? half_row(blockIdx.x) : blockIdx.x + 1;
     const uint32_t half = 1u << n2;
     const T *src = (c1 >= (1u << n1)) ? p + z * a.strideN + ((size_t)(c1 - (1u << n1)) << n2)
                                       : F1 + z * a.strideN + ((size_t)c1 << n2);
-    for (uint32_t e = threadIdx.x; e < half; e += SW_THREADS) {
-        buf[half + e] = src[e];
-        buf[e] = (T)0;
+    if (!HALF) {
+        for (uint32_t e = threadIdx.x; e < half; e += SW_THREADS) {
+            buf[half + e] = src[e];
+            buf[e] = (T)0;
+        }
+    } else {
+        // columns x2 >= 2^(n2-1) of row c1 are the complement row at column cpl(x2)
+        const uint32_t cc = cpl_code(c1), hh = half >> 1, full2 = half - 1u;
+        const T *srcm = (cc >= (1u << n1)) ? p + z * a.strideN + ((size_t)(cc - (1u << n1)) << n2)
+                                           : F1 + z * a.strideN + ((size_t)cc << n2);
+        for (uint32_t e = threadIdx.x; e < half; e += SW_THREADS) {
+            buf[half + e] = (e < hh) ? src[e] : srcm[full2 - e];
+            buf[e] = (T)0;
+        }
     }
     __syncthreads();
     lsweep_fwd_any<T, R>(buf, n2, 0);
@@ -513,7 +541,7 @@ __global__ void __launch_bounds__(SW_THREADS) k_rows_fwd(SweepArgs a, const T *p
 }
 
 // combine: F_n(y) = sum over splits of the two passes' outputs; q_k = F_n / C(n,k)
-template <typename T>
+template <typename T, bool HALF>
 __global__ void k_combine(SweepArgs a, const T *p, const T *F1, const T *Tm, const T *Ts, T *q, T *L, int mode) {
     const int z = blockIdx.y;
     if (a.inst[z * INST_STRIDE + I_ACTIVE] == 0.0) return;
@@ -521,8 +549,10 @@ __global__ void k_combine(SweepArgs a, const T *p, const T *F1, const T *Tm, con
     const T *pz = p + z * a.strideN, *Fz = F1 + z * a.strideN, *Tmz = Tm + z * a.strideM;
     const T *Tsz = Ts + z * ((size_t)32 << (n1 + 1));
     T *qz = q + z * a.strideM, *Lz = L + z * a.strideM;
-    const uint32_t total = 2u << n;
-    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < total; c += gridDim.x * blockDim.x) {
+    const uint32_t total = HALF ? (1u << n) : (2u << n);
+    const uint32_t hh = 1u << (n2 - 1), full2 = (1u << n2) - 1u;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const uint32_t c = HALF ? half_row(t) : t;
         if (c == 0) continue;
         const int k = bitlen32(c) - 1;
         const uint32_t y = c ^ (1u << k);
@@ -530,31 +560,42 @@ __global__ void k_combine(SweepArgs a, const T *p, const T *F1, const T *Tm, con
         T acc = (T)0;
         for (int j = jlo; j <= jhi; j++) {
             const int l = k - j;
-            const uint32_t c1 = (1u << j) | (y >> l);
-            const uint32_t u2 = y & ((1u << l) - 1u);
+            uint32_t c1 = (1u << j) | (y >> l);
+            uint32_t u2 = y & ((1u << l) - 1u);
             const uint32_t c2 = (1u << l) | u2;
             T v;
-            if (l == n2) v = (c1 >= (1u << n1)) ? pz[((size_t)(c1 - (1u << n1)) << n2) | u2] : Fz[((size_t)c1 << n2) | u2];
-            else if (c2 < 32) v = Tsz[((size_t)c2 << (n1 + 1)) + c1];
+            if (l == n2) {
+                if (HALF && u2 >= hh) {  // complement column of the complement row
+                    c1 = cpl_code(c1);
+                    u2 = full2 - u2;
+                }
+                v = (c1 >= (1u << n1)) ? pz[((size_t)(c1 - (1u << n1)) << n2) | u2] : Fz[((size_t)c1 << n2) | u2];
+            } else if (c2 < 32) v = Tsz[((size_t)c2 << (n1 + 1)) + c1];
             else v = Tmz[((size_t)c1 << n2) + c2];
             acc += v;
         }
         T qv = acc * (T)a.inv_binom[k];
+        T lv = log2_t<T>(mode == MODE_CERT ? fmin(qv, (T)1) : fmax(qv, (T)a.q_floor));
         qz[c] = qv;
-        Lz[c] = log2_t<T>(mode == MODE_CERT ? fmin(qv, (T)1) : fmax(qv, (T)a.q_floor));
+        Lz[c] = lv;
+        if (HALF && k > 0) {
+            const uint32_t cm = cpl_code(c);
+            qz[cm] = qv;
+            Lz[cm] = lv;
+        }
     }
 }
 
 // pass 2 adjoint (rows): gather omega_k L(code c1 . c2) over the row, adjoint
 // sweep over x2, write the row's top half to Gb[c1][x2].
-template <typename T, int R>
+template <typename T, int R, bool HALF>
 __global__ void __launch_bounds__(SW_THREADS) k_rows_adj(SweepArgs a, const T *Lsrc, const T *omega, T *Gb) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *buf = reinterpret_cast<T *>(smem_raw);
     const int z = blockIdx.y;
     if (a.inst[z * INST_STRIDE + I_ACTIVE] == 0.0) return;
     const int n1 = a.n1, n2 = a.n2, n = a.n;
-    const uint32_t c1 = blockIdx.x + 1;
+    const uint32_t c1 = HALF ? half_row(blockIdx.x) : blockIdx.x + 1;
     const int j = bitlen32(c1) - 1;
     const T *Lz = Lsrc + z * a.strideM;
     const T *om = omega + z * (n + 1);
@@ -586,7 +627,7 @@ struct EpiArgs {
 
 // pass 1 adjoint (columns): load Gb (or omega L directly when n2 == 0), adjoint
 // sweep over x1, then the epilogue D_x = -Hb(x) - G(x) and block partials.
-template <typename T, int R>
+template <typename T, int R, bool HALF>
 __global__ void __launch_bounds__(SW_THREADS) k_cols_adj(SweepArgs a, EpiArgs ep, const T *Gb, const T *Lsrc,
                                                           const T *omega, int mode) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -601,13 +642,31 @@ __global__ void __launch_bounds__(SW_THREADS) k_cols_adj(SweepArgs a, EpiArgs ep
     const uint32_t nall = (2u << n1) << lw;
     if (n2 > 0) {
         const T *Gz = Gb + z * a.strideM;
+        const uint32_t full2 = (1u << n2) - 1u;
         if (lw >= 2) {
 #pragma unroll 4
             for (uint32_t e = 4 * threadIdx.x; e < nall; e += 4 * SW_THREADS) {
                 uint32_t row = e >> lw, c = e & (w - 1u);
                 T v[4] = {(T)0, (T)0, (T)0, (T)0};
-                if (row) ld4(Gz + (((size_t)row << n2) | (col0 + c)), v);
+                if (row) {
+                    if (!HALF || in_h1(row)) {
+                        ld4(Gz + (((size_t)row << n2) | (col0 + c)), v);
+                    } else {
+                        // rows outside H1: complement row, complement columns (reversed)
+                        T t[4];
+                        ld4(Gz + (((size_t)cpl_code(row) << n2) | (full2 - (col0 + c) - 3u)), t);
+                        v[0] = t[3]; v[1] = t[2]; v[2] = t[1]; v[3] = t[0];
+                    }
+                }
                 st4(buf + e, v);
+            }
+        } else if (HALF) {
+            for (uint32_t e = threadIdx.x; e < nall; e += SW_THREADS) {
+                uint32_t row = e >> lw, c = e & (w - 1u);
+                T v = (T)0;
+                if (row) v = in_h1(row) ? Gz[((size_t)row << n2) | (col0 + c)]
+                                        : Gz[((size_t)cpl_code(row) << n2) | (full2 - (col0 + c))];
+                buf[e] = v;
             }
         } else {
             for (uint32_t e = threadIdx.x; e < nall; e += SW_THREADS) {
@@ -686,7 +745,7 @@ __global__ void __launch_bounds__(SW_THREADS) k_cols_adj(SweepArgs a, EpiArgs ep
         }
     }
     if (mode == MODE_ITER) {
-        sZ = (double)tZ;
+        sZ = (double)tZ * (HALF ? 2.0 : 1.0);  // each column also stands for its complement
         mD = (double)tM;
     }
     double s1 = block_sum<T>(sZ, red);
@@ -793,17 +852,19 @@ Sched make_sched(int n, int elem_bytes, int n2_override, int w_override) {
 template <typename T>
 cudaError_t prepare_all(size_t cols_bytes, size_t rows_bytes) {
     cudaError_t err = cudaSuccess;
-#define PREP_ONE(RR)                                                                                             \
+#define PREP_ONE_H(RR, H)                                                                                        \
     if (RR <= rmax_fwd<T>()) {                                                                                   \
-        if (err == cudaSuccess) err = allow_smem(k_cols_fwd<T, (RR <= rmax_fwd<T>() ? RR : 1)>, cols_bytes);    \
-        if (err == cudaSuccess) err = allow_smem(k_rows_fwd<T, (RR <= rmax_fwd<T>() ? RR : 1)>, rows_bytes);    \
+        if (err == cudaSuccess) err = allow_smem(k_cols_fwd<T, (RR <= rmax_fwd<T>() ? RR : 1), H>, cols_bytes); \
+        if (err == cudaSuccess) err = allow_smem(k_rows_fwd<T, (RR <= rmax_fwd<T>() ? RR : 1), H>, rows_bytes); \
     }                                                                                                            \
     if (RR <= rmax_adj<T>()) {                                                                                   \
-        if (err == cudaSuccess) err = allow_smem(k_cols_adj<T, (RR <= rmax_adj<T>() ? RR : 1)>, cols_bytes);    \
-        if (err == cudaSuccess) err = allow_smem(k_rows_adj<T, (RR <= rmax_adj<T>() ? RR : 1)>, rows_bytes);    \
+        if (err == cudaSuccess) err = allow_smem(k_cols_adj<T, (RR <= rmax_adj<T>() ? RR : 1), H>, cols_bytes); \
+        if (err == cudaSuccess) err = allow_smem(k_rows_adj<T, (RR <= rmax_adj<T>() ? RR : 1), H>, rows_bytes); \
     }
+#define PREP_ONE(RR) PREP_ONE_H(RR, false) PREP_ONE_H(RR, true)
     PREP_ONE(1) PREP_ONE(2) PREP_ONE(4) PREP_ONE(8) PREP_ONE(16) PREP_ONE(32) PREP_ONE(64)
 #undef PREP_ONE
+#undef PREP_ONE_H
     return err;
 }
 
@@ -816,42 +877,63 @@ bdc_status sweep_prepare(bdc_engine *e, PrecBuf<T> &b) {
     return BDC_OK;
 }
 
+bool half_possible(const Sched &s) { return s.n2 > 0 && s.lw < s.n2 && s.n1 >= 1; }
+
 template <typename T>
-bdc_status sweep_forward(bdc_engine *e, PrecBuf<T> &b, const T *p_src, int apply_update, int mode) {
+bdc_status sweep_forward(bdc_engine *e, PrecBuf<T> &b, const T *p_src, int apply_update, int mode, bool half) {
     SweepArgs a = make_args(e, b);
     const Sched &s = b.s;
+    half = half && half_possible(s);
     size_t sm1 = tile_bytes_cols<T>(s);
     T *p = const_cast<T *>(p_src);
-    dim3 g1(s.nblk_cols, e->nd);
+    dim3 g1(half ? s.nblk_cols / 2 : s.nblk_cols, e->nd);
     const int rc = r_of(((size_t)1 << s.n1) << s.lw);
-    SW_WITH_R(rmax_fwd<T>(), rc,
-              (k_cols_fwd<T, R><<<g1, SW_THREADS, sm1, e->stream>>>(a, p, b.D, b.F1, b.q, b.L, apply_update, mode)));
+    if (half)
+        SW_WITH_R(rmax_fwd<T>(), rc, (k_cols_fwd<T, R, true><<<g1, SW_THREADS, sm1, e->stream>>>(
+                                         a, p, b.D, b.F1, b.q, b.L, apply_update, mode)));
+    else
+        SW_WITH_R(rmax_fwd<T>(), rc, (k_cols_fwd<T, R, false><<<g1, SW_THREADS, sm1, e->stream>>>(
+                                         a, p, b.D, b.F1, b.q, b.L, apply_update, mode)));
     e->launches++; stage_mark(e, "cols_fwd");
     BDC_CUDA_TRY(cudaGetLastError());
     if (s.n2 > 0) {
         size_t sm2 = tile_bytes_rows<T>(s);
-        dim3 g2((2u << s.n1) - 1u, e->nd);
+        dim3 g2(half ? (1u << s.n1) : (2u << s.n1) - 1u, e->nd);
         const int rr = r_of((size_t)1 << s.n2);
-        SW_WITH_R(rmax_fwd<T>(), rr, (k_rows_fwd<T, R><<<g2, SW_THREADS, sm2, e->stream>>>(a, p, b.F1, b.Tm, b.Ts)));
+        if (half)
+            SW_WITH_R(rmax_fwd<T>(), rr,
+                      (k_rows_fwd<T, R, true><<<g2, SW_THREADS, sm2, e->stream>>>(a, p, b.F1, b.Tm, b.Ts)));
+        else
+            SW_WITH_R(rmax_fwd<T>(), rr,
+                      (k_rows_fwd<T, R, false><<<g2, SW_THREADS, sm2, e->stream>>>(a, p, b.F1, b.Tm, b.Ts)));
         e->launches++; stage_mark(e, "rows_fwd");
         BDC_CUDA_TRY(cudaGetLastError());
-        int nb = (int)std::min<size_t>(((size_t)2 << e->n) / 256 + 1, 148 * 16);
+        size_t outs = half ? ((size_t)1 << e->n) : ((size_t)2 << e->n);
+        int nb = (int)std::min<size_t>(outs / 256 + 1, 148 * 16);
         dim3 g3(nb, e->nd);
-        k_combine<T><<<g3, 256, 0, e->stream>>>(a, p, b.F1, b.Tm, b.Ts, b.q, b.L, mode); e->launches++; stage_mark(e, "combine");
+        if (half) k_combine<T, true><<<g3, 256, 0, e->stream>>>(a, p, b.F1, b.Tm, b.Ts, b.q, b.L, mode);
+        else k_combine<T, false><<<g3, 256, 0, e->stream>>>(a, p, b.F1, b.Tm, b.Ts, b.q, b.L, mode);
+        e->launches++; stage_mark(e, "combine");
         BDC_CUDA_TRY(cudaGetLastError());
     }
     return BDC_OK;
 }
 
 template <typename T>
-bdc_status sweep_adjoint(bdc_engine *e, PrecBuf<T> &b, const T *Lsrc, const T *omega, T *Dout, int mode) {
+bdc_status sweep_adjoint(bdc_engine *e, PrecBuf<T> &b, const T *Lsrc, const T *omega, T *Dout, int mode, bool half) {
     SweepArgs a = make_args(e, b);
     const Sched &s = b.s;
+    half = half && half_possible(s);
     if (s.n2 > 0) {
         size_t sm2 = tile_bytes_rows<T>(s);
-        dim3 g2((2u << s.n1) - 1u, e->nd);
+        dim3 g2(half ? (1u << s.n1) : (2u << s.n1) - 1u, e->nd);
         const int rr = r_of((size_t)2 << s.n2);
-        SW_WITH_R(rmax_adj<T>(), rr, (k_rows_adj<T, R><<<g2, SW_THREADS, sm2, e->stream>>>(a, Lsrc, omega, b.Gb)));
+        if (half)
+            SW_WITH_R(rmax_adj<T>(), rr,
+                      (k_rows_adj<T, R, true><<<g2, SW_THREADS, sm2, e->stream>>>(a, Lsrc, omega, b.Gb)));
+        else
+            SW_WITH_R(rmax_adj<T>(), rr,
+                      (k_rows_adj<T, R, false><<<g2, SW_THREADS, sm2, e->stream>>>(a, Lsrc, omega, b.Gb)));
         e->launches++; stage_mark(e, "rows_adj");
         BDC_CUDA_TRY(cudaGetLastError());
     }
@@ -867,10 +949,14 @@ bdc_status sweep_adjoint(bdc_engine *e, PrecBuf<T> &b, const T *Lsrc, const T *o
         ep.eH_scale = 1.01 * (m * ep.u / (1.0 - m * ep.u)) + 1.01 * ep.u;
     }
     size_t sm1 = tile_bytes_cols<T>(s);
-    dim3 g1(s.nblk_cols, e->nd);
+    dim3 g1(half ? s.nblk_cols / 2 : s.nblk_cols, e->nd);
     const int rc = r_of(((size_t)2 << s.n1) << s.lw);
-    SW_WITH_R(rmax_adj<T>(), rc,
-              (k_cols_adj<T, R><<<g1, SW_THREADS, sm1, e->stream>>>(a, ep, b.Gb, Lsrc, omega, mode)));
+    if (half)
+        SW_WITH_R(rmax_adj<T>(), rc,
+                  (k_cols_adj<T, R, true><<<g1, SW_THREADS, sm1, e->stream>>>(a, ep, b.Gb, Lsrc, omega, mode)));
+    else
+        SW_WITH_R(rmax_adj<T>(), rc,
+                  (k_cols_adj<T, R, false><<<g1, SW_THREADS, sm1, e->stream>>>(a, ep, b.Gb, Lsrc, omega, mode)));
     e->launches++; stage_mark(e, "cols_adj");
     BDC_CUDA_TRY(cudaGetLastError());
     return BDC_OK;
@@ -878,10 +964,11 @@ bdc_status sweep_adjoint(bdc_engine *e, PrecBuf<T> &b, const T *Lsrc, const T *o
 
 template bdc_status sweep_prepare<float>(bdc_engine *, PrecBuf<float> &);
 template bdc_status sweep_prepare<double>(bdc_engine *, PrecBuf<double> &);
-template bdc_status sweep_forward<float>(bdc_engine *, PrecBuf<float> &, const float *, int, int);
-template bdc_status sweep_forward<double>(bdc_engine *, PrecBuf<double> &, const double *, int, int);
-template bdc_status sweep_adjoint<float>(bdc_engine *, PrecBuf<float> &, const float *, const float *, float *, int);
-template bdc_status sweep_adjoint<double>(bdc_engine *, PrecBuf<double> &, const double *, const double *, double *, int);
+template bdc_status sweep_forward<float>(bdc_engine *, PrecBuf<float> &, const float *, int, int, bool);
+template bdc_status sweep_forward<double>(bdc_engine *, PrecBuf<double> &, const double *, int, int, bool);
+template bdc_status sweep_adjoint<float>(bdc_engine *, PrecBuf<float> &, const float *, const float *, float *, int, bool);
+template bdc_status sweep_adjoint<double>(bdc_engine *, PrecBuf<double> &, const double *, const double *, double *, int,
+                                          bool);
 
 // ---------------------------------------------------------------------------
 // Output marginal without any device allocation.
@@ -987,15 +1074,15 @@ extern "C" bdc_status bdc_output_marginal_static(int n, double d, const double *
     double *p = const_cast<double *>(p_dev);  // read only: no update is applied
     const int rc = r_of(((size_t)1 << s.n1) << s.lw);
     SW_WITH_R(rmax_fwd<double>(), rc,
-              (k_cols_fwd<double, R><<<dim3(s.nblk_cols, 1), SW_THREADS, tile_bytes_cols<double>(s), st>>>(
+              (k_cols_fwd<double, R, false><<<dim3(s.nblk_cols, 1), SW_THREADS, tile_bytes_cols<double>(s), st>>>(
                   a, p, p, F1, q_dev, L, 0, MODE_DUAL)));
     if (s.n2 > 0) {
         const int rr = r_of((size_t)1 << s.n2);
         SW_WITH_R(rmax_fwd<double>(), rr,
-                  (k_rows_fwd<double, R><<<dim3((2u << s.n1) - 1u, 1), SW_THREADS, tile_bytes_rows<double>(s), st>>>(
+                  (k_rows_fwd<double, R, false><<<dim3((2u << s.n1) - 1u, 1), SW_THREADS, tile_bytes_rows<double>(s), st>>>(
                       a, p, F1, Tm, Ts)));
         int nb = (int)std::min<size_t>((2 * N) / 256 + 1, 148 * 16);
-        k_combine<double><<<dim3(nb, 1), 256, 0, st>>>(a, p, F1, Tm, Ts, q_dev, L, MODE_DUAL);
+        k_combine<double, false><<<dim3(nb, 1), 256, 0, st>>>(a, p, F1, Tm, Ts, q_dev, L, MODE_DUAL);
     }
     BDC_CUDA_TRY(cudaGetLastError());
     return BDC_OK;

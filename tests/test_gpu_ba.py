@@ -155,3 +155,51 @@ def test_precision_switch_and_literal_agree():
     assert np.all(np.abs(hlo - ref["lower"]) <= 1e-11)
     assert np.all(np.abs(hup - ref["upper"]) <= 1e-11)
     eng.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 2e-5)])
+def test_half_mode_iterations_match_oracle(prec, tol):
+    # a forced split schedule at n = 10 runs the complement half mode
+    n, d, T = 10, 0.6, 40
+    ref = oracle.ba_bdc(n, d, T)
+    eng = _engine(n, [d], sched_n2_fp32=6, sched_w_fp32=4, sched_n2_fp64=7, sched_w_fp64=2)
+    eng.iterate(T, -1.0, prec, "sweep")
+    hlo, hup = eng.history(0)
+    assert np.all(np.abs(hlo - ref["lower"]) <= tol * np.maximum(1.0, np.abs(ref["lower"])))
+    assert np.all(np.abs(hup - ref["upper"]) <= tol * np.maximum(1.0, np.abs(ref["upper"])))
+    p = eng.get_p()[0]
+    assert np.all(np.abs(p - ref["p"]) <= (1e-9 if prec == "fp64" else 2e-3) * ref["p"])
+    eng.close()
+
+
+def test_half_and_full_mode_agree():
+    import paper_2604_05867_b300 as bdc
+    n, d, T = 16, 0.55, 30
+    a = _engine(n, [d, 0.8])
+    b = bdc.Engine(n, [d, 0.8], options=bdc.default_options(use_half=0))
+    a.iterate(T, -1.0, "fp64", "sweep")
+    b.iterate(T, -1.0, "fp64", "sweep")
+    for z in range(2):
+        la, ua = a.history(z)
+        lb, ub = b.history(z)
+        assert np.all(np.abs(la - lb) <= 1e-11) and np.all(np.abs(ua - ub) <= 1e-11)
+    pa, pb = a.get_p(), b.get_p()
+    assert np.all(np.abs(pa - pb) <= 1e-11 * pb)
+    a.close()
+    b.close()
+
+
+def test_asymmetric_p_switches_off_symmetry_shortcuts():
+    n, d, T = 10, 0.45, 20
+    rng = np.random.default_rng(7)
+    p0 = rng.dirichlet(np.ones(1 << n))
+    ref = oracle.ba_bdc(n, d, T, p0=p0)
+    eng = _engine(n, [d], sched_n2_fp64=7, sched_w_fp64=2)
+    eng.set_p(p0)
+    eng.iterate(T, -1.0, "fp64", "sweep")
+    hlo, hup = eng.history(0)
+    assert np.all(np.abs(hlo - ref["lower"]) <= 1e-11) and np.all(np.abs(hup - ref["upper"]) <= 1e-11)
+    import paper_2604_05867_b300 as bdc
+    with pytest.raises(bdc.BdcError):
+        eng.iterate(1, -1.0, "fp64", "literal")
+    eng.close()
