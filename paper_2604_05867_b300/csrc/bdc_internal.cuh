@@ -175,7 +175,8 @@ bdc_status launch_literal_D(bdc_engine *e);
 template <typename T>
 bdc_status sweep_prepare(bdc_engine *e, PrecBuf<T> &b);
 template <typename T>
-bdc_status sweep_forward(bdc_engine *e, PrecBuf<T> &b, const T *p_src, int apply_update, int mode, bool half = false);
+bdc_status sweep_forward(bdc_engine *e, PrecBuf<T> &b, const T *p_src, int apply_update, int mode, bool half = false,
+                         bool sym_rev = false);
 template <typename T>
 bdc_status sweep_adjoint(bdc_engine *e, PrecBuf<T> &b, const T *Lsrc, const T *omega, T *Dout, int mode,
                          bool half = false);
@@ -221,6 +222,12 @@ enum { MODE_ITER = 0, MODE_CERT = 1, MODE_DIV = 2, MODE_DUAL = 3, MODE_DUAL_D = 
 // device helpers
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int bitlen32(uint32_t v) { return 32 - __clz(v); }
+
+// instance flags (I_ACTIVE, I_PENDING, I_SYMNEED) hold exactly 1.0 or 0.0;
+// testing their bit pattern keeps FP64 instructions out of FP32 kernels
+__device__ __forceinline__ bool flag_set(const double *inst, int slot) {
+    return __double_as_longlong(inst[slot]) != 0;
+}
 
 __device__ __forceinline__ uint32_t rev_bits(uint32_t v, int L) {
     return L == 0 ? 0u : (__brev(v) >> (32 - L));

@@ -419,6 +419,11 @@ extern "C" bdc_status bdc_bind(bdc_engine *e, void *ws, size_t bytes, void *stre
 // ---------------------------------------------------------------------------
 // complement half mode left: rebuild the upper half of p and D
 static bdc_status unhalf(bdc_engine *e) {
+    // half-mode iterations leave D un-averaged (the next forward pass averages
+    // it on the fly): average the current precision's D before mirroring
+    const bool sym = e->opt.symmetrize && e->orbit_ok;
+    if (sym && e->cur == 0 && e->half_active[0]) BDC_TRY(launch_symmetrize<float>(e, e->f32.D, e->half_n2[0]));
+    if (sym && e->cur == 1 && e->half_active[1]) BDC_TRY(launch_symmetrize<double>(e, e->f64.D, e->half_n2[1]));
     if (e->half_active[0]) {
         BDC_TRY(launch_mirror_half<float>(e, e->f32.p, e->half_n2[0]));
         BDC_TRY(launch_mirror_half<float>(e, e->f32.D, e->half_n2[0]));
@@ -480,10 +485,13 @@ static bdc_status iter_sweep(bdc_engine *e, PrecBuf<T> &b, int prec) {
     // complement half mode while p is complement-invariant
     const bool half = e->opt.use_half && e->half_ok && half_possible(b.s);
     if (!half && e->half_active[prec]) BDC_TRY(unhalf(e));
-    BDC_TRY(sweep_forward<T>(e, b, b.p, 1, MODE_ITER, half));
+    // orbit mean of D: in half mode fused into the next forward pass (and into
+    // unhalf), otherwise a pass of its own
+    const bool sym = e->opt.symmetrize && e->orbit_ok;
+    BDC_TRY(sweep_forward<T>(e, b, b.p, 1, MODE_ITER, half, half && sym));
     BDC_TRY(sweep_adjoint<T>(e, b, b.L, b.omega, b.D, MODE_ITER, half));
     BDC_TRY(launch_finalize<T>(e, b, MODE_ITER, 0, half ? b.s.nblk_cols / 2 : b.s.nblk_cols));
-    if (e->opt.symmetrize && e->orbit_ok) BDC_TRY(launch_symmetrize<T>(e, b.D, half ? b.s.n2 : 0));
+    if (sym && !half) BDC_TRY(launch_symmetrize<T>(e, b.D, 0));
     if (half) {
         e->half_active[prec] = true;
         e->half_n2[prec] = b.s.n2;

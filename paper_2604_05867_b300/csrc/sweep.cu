@@ -371,6 +371,36 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
     return s;
 }
 
+// the same reductions in the working precision, sum and maximum together
+// (one shared-memory round trip; fixed tree, so deterministic); thread 0
+// gets the block's values.  red holds 2 * SW_THREADS / 32 elements.
+template <typename T>
+__device__ __forceinline__ void block_sum_max_t(T &s, T &m, T *red) {
+    const unsigned FULL = 0xffffffffu;
+    constexpr int NW = SW_THREADS / 32;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(FULL, s, o);
+        T t = __shfl_xor_sync(FULL, m, o);
+        m = t > m ? t : m;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[threadIdx.x >> 5] = s;
+        red[NW + (threadIdx.x >> 5)] = m;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < NW ? red[threadIdx.x] : (T)0;
+        m = threadIdx.x < NW ? red[NW + threadIdx.x] : (T)-INFINITY;
+#pragma unroll
+        for (int o = NW / 2; o > 0; o >>= 1) {
+            s += __shfl_xor_sync(FULL, s, o);
+            T t = __shfl_xor_sync(FULL, m, o);
+            m = t > m ? t : m;
+        }
+    }
+}
+
 __device__ __forceinline__ double block_max(double v, double *red) {
     const unsigned FULL = 0xffffffffu;
 #pragma unroll
@@ -409,7 +439,51 @@ struct SweepArgs {
     int maxblk;
     double q_floor;
     const double *inv_binom;  // [n+1]
+    // FP32 copies of the two constants, so FP32 kernels convert nothing
+    float q_floor_f;
+    float inv_binom_f[BDC_MAXN + 2];
 };
+
+template <typename T>
+__device__ __forceinline__ T inv_binom_t(const SweepArgs &a, int k);
+template <>
+__device__ __forceinline__ float inv_binom_t<float>(const SweepArgs &a, int k) { return a.inv_binom_f[k]; }
+template <>
+__device__ __forceinline__ double inv_binom_t<double>(const SweepArgs &a, int k) { return a.inv_binom[k]; }
+template <typename T>
+__device__ __forceinline__ T q_floor_t(const SweepArgs &a);
+template <>
+__device__ __forceinline__ float q_floor_t<float>(const SweepArgs &a) { return a.q_floor_f; }
+template <>
+__device__ __forceinline__ double q_floor_t<double>(const SweepArgs &a) { return a.q_floor; }
+
+// Orbit mean fused into the update (complement half mode).  In half mode
+// D(cpl x) = D(x), so the mean of D over the orbit {x, cpl x, rev x, cpl rev x}
+// is (D(x) + D(rev x)) / 2, which is symmetric in its two terms: every orbit
+// member gets the same bits.  For a column tile (all x1, columns x2 in
+// [col0, col0 + w)) the reversed inputs rev(x1 x2) = rev(x2) rev(x1) fill w
+// contiguous runs of 2^n1 elements, so they are read coalesced and staged in
+// shared memory at the position of x1 = rev(o).  The staged layout XORs the
+// top sb bits of x1 into its low bits: the staging writes of one warp then
+// hit distinct banks, and each 4-column group stays 16-byte aligned.
+__device__ __forceinline__ int swz_bits(int n1, int lw) { return min(max(0, 5 - lw), n1 / 2); }
+__device__ __forceinline__ uint32_t swz_pos(uint32_t x1, uint32_t c, int lw, int n1, int sb) {
+    return ((x1 << lw) | c) ^ (((x1 >> (n1 - sb)) & ((1u << sb) - 1u)) << lw);
+}
+
+template <typename T>
+__device__ __forceinline__ void stage_rev_D(T *buf, const T *Dz, int n, int n1, int n2, int lw, uint32_t col0,
+                                            int sb) {
+    const uint32_t ntop = (1u << n1) << lw, cm = (1u << lw) - 1u;
+    const uint32_t full = (1u << n) - 1u;
+#pragma unroll 8
+    for (uint32_t idx = threadIdx.x; idx < ntop; idx += SW_THREADS) {
+        const uint32_t o = idx >> lw, c = idx & cm;
+        uint32_t j = (rev_bits(col0 + c, n2) << n1) | o;
+        if ((j >> (n2 - 1)) & 1u) j ^= full;  // held as its complement
+        buf[swz_pos(rev_bits(o, n1), c, lw, n1, sb)] = Dz[j];
+    }
+}
 
 // ---------------------------------------------------------------------------
 // pass 1 forward (columns): tile = all x1 x (1<<lw) consecutive x2.
@@ -418,22 +492,30 @@ struct SweepArgs {
 // ---------------------------------------------------------------------------
 template <typename T, int R, bool HALF>
 __global__ void __launch_bounds__(SW_THREADS) k_cols_fwd(SweepArgs a, T *p, const T *D, T *F1, T *q, T *L,
-                                                          int apply_update, int mode) {
+                                                          int apply_update, int mode, int sym_rev) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *buf = reinterpret_cast<T *>(smem_raw);
-    __shared__ double red[SW_THREADS / 32];
+    __shared__ T red[2 * SW_THREADS / 32];
     const int z = blockIdx.y;
     const double *inst = a.inst + z * INST_STRIDE;
-    if (inst[I_ACTIVE] == 0.0) return;
+    if (!flag_set(inst, I_ACTIVE)) return;
     const int n1 = a.n1, n2 = a.n2, lw = a.lw;
     const uint32_t w = 1u << lw;
     const uint32_t col0 = blockIdx.x << lw;
     T *pz = p + z * a.strideN;
     const T *Dz = D + z * a.strideN;
-    const bool upd = apply_update && inst[I_PENDING] != 0.0;
+    const bool upd = apply_update && flag_set(inst, I_PENDING);
     const T shift = (T)inst[I_SHIFT];
     const uint32_t ntop = (1u << n1) << lw;
-    T psum = (T)0;  // per-thread partial in the working precision, block sum in FP64
+    // orbit mean fused here (half mode, D not yet averaged): the bottom half of
+    // the tile holds D(rev x) until each value is used, then is zeroed by its user
+    const bool symr = HALF && sym_rev && upd && flag_set(inst, I_SYMNEED);
+    const int sb = swz_bits(n1, lw);
+    if (symr) {
+        stage_rev_D<T>(buf, Dz, a.n, n1, n2, lw, col0, sb);
+        __syncthreads();
+    }
+    T psum = (T)0;  // per-thread partial in the working precision
     if (lw >= 2) {
         // 4 consecutive columns of one row per step: 16-byte global accesses
 #pragma unroll 4
@@ -441,16 +523,24 @@ __global__ void __launch_bounds__(SW_THREADS) k_cols_fwd(SweepArgs a, T *p, cons
             uint32_t x1 = e >> lw, c = e & (w - 1u);
             size_t x = ((size_t)x1 << n2) | (col0 + c);
             T v[4], dv[4];
+            const T zero[4] = {(T)0, (T)0, (T)0, (T)0};
             ld4(pz + x, v);
             if (upd) {
                 ld4(Dz + x, dv);
+                if (symr) {
+                    T dr[4];
+                    const uint32_t sp = swz_pos(x1, c, lw, n1, sb);
+                    ld4(buf + sp, dr);
+                    st4(buf + sp, zero);
+#pragma unroll
+                    for (int k = 0; k < 4; k++) dv[k] = (dv[k] + dr[k]) * (T)0.5;
+                }
 #pragma unroll
                 for (int k = 0; k < 4; k++) v[k] = v[k] * exp2_t<T>(dv[k] - shift);
                 st4(pz + x, v);
             }
             st4(buf + ntop + e, v);
-            T zero[4] = {(T)0, (T)0, (T)0, (T)0};
-            st4(buf + e, zero);
+            if (!symr) st4(buf + e, zero);
             psum += (v[0] + v[1]) + (v[2] + v[3]);
         }
     } else {
@@ -459,19 +549,26 @@ __global__ void __launch_bounds__(SW_THREADS) k_cols_fwd(SweepArgs a, T *p, cons
             size_t x = ((size_t)x1 << n2) | (col0 + c);
             T v = pz[x];
             if (upd) {
-                v = v * exp2_t<T>(Dz[x] - shift);
+                T dv = Dz[x];
+                if (symr) {
+                    const uint32_t sp = swz_pos(x1, c, lw, n1, sb);
+                    dv = (dv + buf[sp]) * (T)0.5;
+                    buf[sp] = (T)0;
+                }
+                v = v * exp2_t<T>(dv - shift);
                 pz[x] = v;
             }
             buf[ntop + e] = v;
-            buf[e] = (T)0;
+            if (!symr) buf[e] = (T)0;
             psum += v;
         }
     }
-    // in half mode each column x2 also stands for its complement column
-    double s = block_sum<T>((double)psum * (HALF ? 2.0 : 1.0), red);
+    T pmax = (T)0;
+    block_sum_max_t<T>(psum, pmax, red);
     if (threadIdx.x == 0 && (mode == MODE_ITER || mode == MODE_DIV)) {
         double *pp = a.part + ((size_t)z * 2 + 0) * a.maxblk * 4 + blockIdx.x * 4;
-        pp[0] = s;
+        // in half mode each column x2 also stands for its complement column
+        pp[0] = (double)psum * (HALF ? 2.0 : 1.0);
     }
     __syncthreads();
     lsweep_fwd_any<T, R>(buf, n1, lw);
@@ -495,9 +592,9 @@ __global__ void __launch_bounds__(SW_THREADS) k_cols_fwd(SweepArgs a, T *p, cons
         T *qz = q + z * a.strideM, *Lz = L + z * a.strideM;
         for (uint32_t c = threadIdx.x + 1; c < (2u << n1); c += SW_THREADS) {
             int k = bitlen32(c) - 1;
-            T qv = buf[c] * (T)a.inv_binom[k];
+            T qv = buf[c] * inv_binom_t<T>(a, k);
             qz[c] = qv;
-            Lz[c] = log2_t<T>(mode == MODE_CERT ? fmin(qv, (T)1) : fmax(qv, (T)a.q_floor));
+            Lz[c] = log2_t<T>(mode == MODE_CERT ? fmin(qv, (T)1) : fmax(qv, q_floor_t<T>(a)));
         }
     }
 }
@@ -509,7 +606,7 @@ __global__ void __launch_bounds__(SW_THREADS) k_rows_fwd(SweepArgs a, const T *p
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *buf = reinterpret_cast<T *>(smem_raw);
     const int z = blockIdx.y;
-    if (a.inst[z * INST_STRIDE + I_ACTIVE] == 0.0) return;
+    if (!flag_set(a.inst + z * INST_STRIDE, I_ACTIVE)) return;
     const int n1 = a.n1, n2 = a.n2;
     const uint32_t c1 = HALF ? half_row(blockIdx.x) : blockIdx.x + 1;
     const uint32_t half = 1u << n2;
@@ -544,7 +641,7 @@ __global__ void __launch_bounds__(SW_THREADS) k_rows_fwd(SweepArgs a, const T *p
 template <typename T, bool HALF>
 __global__ void k_combine(SweepArgs a, const T *p, const T *F1, const T *Tm, const T *Ts, T *q, T *L, int mode) {
     const int z = blockIdx.y;
-    if (a.inst[z * INST_STRIDE + I_ACTIVE] == 0.0) return;
+    if (!flag_set(a.inst + z * INST_STRIDE, I_ACTIVE)) return;
     const int n1 = a.n1, n2 = a.n2, n = a.n;
     const T *pz = p + z * a.strideN, *Fz = F1 + z * a.strideN, *Tmz = Tm + z * a.strideM;
     const T *Tsz = Ts + z * ((size_t)32 << (n1 + 1));
@@ -574,8 +671,8 @@ __global__ void k_combine(SweepArgs a, const T *p, const T *F1, const T *Tm, con
             else v = Tmz[((size_t)c1 << n2) + c2];
             acc += v;
         }
-        T qv = acc * (T)a.inv_binom[k];
-        T lv = log2_t<T>(mode == MODE_CERT ? fmin(qv, (T)1) : fmax(qv, (T)a.q_floor));
+        T qv = acc * inv_binom_t<T>(a, k);
+        T lv = log2_t<T>(mode == MODE_CERT ? fmin(qv, (T)1) : fmax(qv, q_floor_t<T>(a)));
         qz[c] = qv;
         Lz[c] = lv;
         if (HALF && k > 0) {
@@ -593,7 +690,7 @@ __global__ void __launch_bounds__(SW_THREADS) k_rows_adj(SweepArgs a, const T *L
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *buf = reinterpret_cast<T *>(smem_raw);
     const int z = blockIdx.y;
-    if (a.inst[z * INST_STRIDE + I_ACTIVE] == 0.0) return;
+    if (!flag_set(a.inst + z * INST_STRIDE, I_ACTIVE)) return;
     const int n1 = a.n1, n2 = a.n2, n = a.n;
     const uint32_t c1 = HALF ? half_row(blockIdx.x) : blockIdx.x + 1;
     const int j = bitlen32(c1) - 1;
@@ -633,9 +730,10 @@ __global__ void __launch_bounds__(SW_THREADS) k_cols_adj(SweepArgs a, EpiArgs ep
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *buf = reinterpret_cast<T *>(smem_raw);
     __shared__ double red[SW_THREADS / 32];
+    __shared__ T redT[2 * SW_THREADS / 32];
     const int z = blockIdx.y;
     const double *inst = a.inst + z * INST_STRIDE;
-    if (inst[I_ACTIVE] == 0.0) return;
+    if (!flag_set(inst, I_ACTIVE)) return;
     const int n1 = a.n1, n2 = a.n2, lw = a.lw, n = a.n;
     const uint32_t w = 1u << lw;
     const uint32_t col0 = blockIdx.x << lw;
@@ -745,8 +843,15 @@ __global__ void __launch_bounds__(SW_THREADS) k_cols_adj(SweepArgs a, EpiArgs ep
         }
     }
     if (mode == MODE_ITER) {
-        sZ = (double)tZ * (HALF ? 2.0 : 1.0);  // each column also stands for its complement
-        mD = (double)tM;
+        block_sum_max_t<T>(tZ, tM, redT);
+        if (threadIdx.x == 0) {
+            double *pp = a.part + ((size_t)z * 2 + 1) * a.maxblk * 4 + blockIdx.x * 4;
+            pp[0] = (double)tZ * (HALF ? 2.0 : 1.0);  // each column also stands for its complement
+            pp[1] = (double)tM;
+            pp[2] = 0.0;
+            pp[3] = -INFINITY;
+        }
+        return;
     }
     double s1 = block_sum<T>(sZ, red);
     double s3 = block_sum<T>(sP, red);
@@ -776,6 +881,12 @@ SweepArgs make_args(bdc_engine *e, PrecBuf<T> &b) {
     a.maxblk = part_maxblk(e);
     a.q_floor = e->opt.q_floor;
     a.inv_binom = e->bk + (size_t)4 * e->nd * (e->n + 1);
+    a.q_floor_f = (float)e->opt.q_floor;
+    double c = 1.0;  // C(n,k), exact in double for n <= 26
+    for (int k = 0; k <= e->n; k++) {
+        a.inv_binom_f[k] = (float)(1.0 / c);
+        c = c * (e->n - k) / (k + 1);
+    }
     return a;
 }
 
@@ -880,7 +991,8 @@ bdc_status sweep_prepare(bdc_engine *e, PrecBuf<T> &b) {
 bool half_possible(const Sched &s) { return s.n2 > 0 && s.lw < s.n2 && s.n1 >= 1; }
 
 template <typename T>
-bdc_status sweep_forward(bdc_engine *e, PrecBuf<T> &b, const T *p_src, int apply_update, int mode, bool half) {
+bdc_status sweep_forward(bdc_engine *e, PrecBuf<T> &b, const T *p_src, int apply_update, int mode, bool half,
+                         bool sym_rev) {
     SweepArgs a = make_args(e, b);
     const Sched &s = b.s;
     half = half && half_possible(s);
@@ -890,10 +1002,10 @@ bdc_status sweep_forward(bdc_engine *e, PrecBuf<T> &b, const T *p_src, int apply
     const int rc = r_of(((size_t)1 << s.n1) << s.lw);
     if (half)
         SW_WITH_R(rmax_fwd<T>(), rc, (k_cols_fwd<T, R, true><<<g1, SW_THREADS, sm1, e->stream>>>(
-                                         a, p, b.D, b.F1, b.q, b.L, apply_update, mode)));
+                                         a, p, b.D, b.F1, b.q, b.L, apply_update, mode, sym_rev ? 1 : 0)));
     else
         SW_WITH_R(rmax_fwd<T>(), rc, (k_cols_fwd<T, R, false><<<g1, SW_THREADS, sm1, e->stream>>>(
-                                         a, p, b.D, b.F1, b.q, b.L, apply_update, mode)));
+                                         a, p, b.D, b.F1, b.q, b.L, apply_update, mode, 0)));
     e->launches++; stage_mark(e, "cols_fwd");
     BDC_CUDA_TRY(cudaGetLastError());
     if (s.n2 > 0) {
@@ -964,8 +1076,8 @@ bdc_status sweep_adjoint(bdc_engine *e, PrecBuf<T> &b, const T *Lsrc, const T *o
 
 template bdc_status sweep_prepare<float>(bdc_engine *, PrecBuf<float> &);
 template bdc_status sweep_prepare<double>(bdc_engine *, PrecBuf<double> &);
-template bdc_status sweep_forward<float>(bdc_engine *, PrecBuf<float> &, const float *, int, int, bool);
-template bdc_status sweep_forward<double>(bdc_engine *, PrecBuf<double> &, const double *, int, int, bool);
+template bdc_status sweep_forward<float>(bdc_engine *, PrecBuf<float> &, const float *, int, int, bool, bool);
+template bdc_status sweep_forward<double>(bdc_engine *, PrecBuf<double> &, const double *, int, int, bool, bool);
 template bdc_status sweep_adjoint<float>(bdc_engine *, PrecBuf<float> &, const float *, const float *, float *, int, bool);
 template bdc_status sweep_adjoint<double>(bdc_engine *, PrecBuf<double> &, const double *, const double *, double *, int,
                                           bool);
@@ -1075,7 +1187,7 @@ extern "C" bdc_status bdc_output_marginal_static(int n, double d, const double *
     const int rc = r_of(((size_t)1 << s.n1) << s.lw);
     SW_WITH_R(rmax_fwd<double>(), rc,
               (k_cols_fwd<double, R, false><<<dim3(s.nblk_cols, 1), SW_THREADS, tile_bytes_cols<double>(s), st>>>(
-                  a, p, p, F1, q_dev, L, 0, MODE_DUAL)));
+                  a, p, p, F1, q_dev, L, 0, MODE_DUAL, 0)));
     if (s.n2 > 0) {
         const int rr = r_of((size_t)1 << s.n2);
         SW_WITH_R(rmax_fwd<double>(), rr,

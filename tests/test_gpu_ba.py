@@ -203,3 +203,30 @@ def test_asymmetric_p_switches_off_symmetry_shortcuts():
     with pytest.raises(bdc.BdcError):
         eng.iterate(1, -1.0, "fp64", "literal")
     eng.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_half_mode_keeps_p_exactly_orbit_invariant(prec):
+    # half-mode iterations average D over each orbit inside the forward pass;
+    # the resulting p must be bit-identical across every orbit, and the run must
+    # match the full-mode run (separate orbit-mean pass)
+    import paper_2604_05867_b300 as bdc
+    n, d, T = 12, 0.35, 25
+    kw = dict(sched_n2_fp32=6, sched_w_fp32=4, sched_n2_fp64=7, sched_w_fp64=2)
+    a = bdc.Engine(n, [d], options=bdc.default_options(**kw))
+    b = bdc.Engine(n, [d], options=bdc.default_options(use_half=0, **kw))
+    a.iterate(T, -1.0, prec, "sweep")
+    b.iterate(T, -1.0, prec, "sweep")
+    pa = a.get_p()[0]
+    x = np.arange(1 << n)
+    full = (1 << n) - 1
+    rx = np.array([int(format(v, "0%db" % n)[::-1], 2) for v in x])
+    assert np.array_equal(pa, pa[x ^ full]) and np.array_equal(pa, pa[rx])
+    pb = b.get_p()[0]
+    ptol, htol = (1e-11, 1e-11) if prec == "fp64" else (2e-3, 2e-5 * n)
+    assert np.all(np.abs(pa - pb) <= ptol * pb)
+    la, ua = a.history(0)
+    lb, ub = b.history(0)
+    assert np.all(np.abs(la - lb) <= htol) and np.all(np.abs(ua - ub) <= htol)
+    a.close()
+    b.close()
