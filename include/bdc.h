@@ -76,6 +76,12 @@ typedef struct {
      * start, Appendix A), compute only half of every sweep and mirror the
      * rest.  Default 1. */
     int use_half;
+    /* Bit mask: run the first forward / last adjoint steps of a sweep tile
+     * in registers (identical arithmetic, fewer shared-memory passes) in the
+     * forward rows pass (1), the adjoint rows pass (2), and, in BA iterations,
+     * the forward (4) and adjoint (8) columns passes, where the tile shape
+     * allows.  Default 15; 0 keeps every step in shared memory. */
+    int use_regsteps;
 } bdc_options;
 
 /* Fill *opt with the defaults above. */

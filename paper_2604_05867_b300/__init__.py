@@ -41,7 +41,8 @@ class Options(ctypes.Structure):
                 ("q_floor", ctypes.c_double), ("certify_mix", ctypes.c_double),
                 ("sched_n2_fp32", ctypes.c_int), ("sched_w_fp32", ctypes.c_int),
                 ("sched_n2_fp64", ctypes.c_int), ("sched_w_fp64", ctypes.c_int),
-                ("enable_literal", ctypes.c_int), ("use_half", ctypes.c_int)]
+                ("enable_literal", ctypes.c_int), ("use_half", ctypes.c_int),
+                ("use_regsteps", ctypes.c_int)]
 
 
 _lib = None

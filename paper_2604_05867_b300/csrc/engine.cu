@@ -238,6 +238,7 @@ extern "C" void bdc_default_options(bdc_options *o) {
     o->certify_mix = 9.313225746154785e-10;  // 2^-30
     o->enable_literal = 1;
     o->use_half = 1;
+    o->use_regsteps = 15;
 }
 
 extern "C" bdc_status bdc_create(int n, const double *d, int nd, const bdc_options *opt, bdc_engine **out) {

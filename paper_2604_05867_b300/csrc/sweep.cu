@@ -38,36 +38,36 @@ constexpr int SW_THREADS = 512;
 // per step it reads the two inserted-bit rows from shared memory, then
 // (after a barrier) publishes its new values.  R is a compile-time bound
 // on the elements per thread: R * SW_THREADS >= 2^nn << lw.
-template <typename T, int R>
-__device__ void lsweep_fwd_reg(T *buf, int nn, int lw) {
+template <typename T, int R, int NT = SW_THREADS>
+__device__ void lsweep_fwd_reg(T *buf, int nn, int lw, int ib = 0) {
     const int tid = threadIdx.x;
     const uint32_t nel = (1u << nn) << lw;
     const uint32_t cmask = (1u << lw) - 1u;
     T own[R];
 #pragma unroll
     for (int j = 0; j < R; j++) {
-        uint32_t e = tid + j * SW_THREADS;
+        uint32_t e = tid + j * NT;
         own[j] = (e < nel) ? buf[e] : (T)0;
     }
-    for (int i = 0; i < nn; i++) {
+    for (int i = ib; i < nn; i++) {
         const int m = nn - i - 1;
         const uint32_t row_lo = 1u << m;
         // read phase: other rows' old values from shared memory, own in registers
 #pragma unroll
         for (int j = 0; j < R; j++) {
-            uint32_t e = tid + j * SW_THREADS;
+            uint32_t e = tid + j * NT;
             uint32_t P = e >> lw;
             if (e < nel && P >= row_lo) {
                 uint32_t c = e & cmask;
                 uint32_t i0 = ((P >> m) << (m + 1)) | (P & (row_lo - 1u));
-                own[j] += buf[(i0 << lw) | c] + buf[((i0 | row_lo) << lw) | c];
+                own[j] = own[j] + buf[(i0 << lw) | c] + buf[((i0 | row_lo) << lw) | c];
             }
         }
         __syncthreads();
         // publish phase
 #pragma unroll
         for (int j = 0; j < R; j++) {
-            uint32_t e = tid + j * SW_THREADS;
+            uint32_t e = tid + j * NT;
             if (e < nel && (e >> lw) >= row_lo) buf[e] = own[j];
         }
         __syncthreads();
@@ -75,27 +75,27 @@ __device__ void lsweep_fwd_reg(T *buf, int nn, int lw) {
 }
 
 // adjoint sweep: every row Q >= 2^(m+1) adds the row cmp(Q) (bit m removed)
-// of the previous level.  Thread t owns e = t + j*SW_THREADS of the whole
-// tile (R * SW_THREADS >= 2^(nn+1) << lw); afterwards rows [2^nn, 2^(nn+1))
+// of the previous level.  Thread t owns e = t + j*NT of the whole
+// tile (R * NT >= 2^(nn+1) << lw); afterwards rows [2^nn, 2^(nn+1))
 // hold the result.
-template <typename T, int R>
-__device__ void lsweep_adj_reg(T *buf, int nn, int lw) {
+template <typename T, int R, int NT = SW_THREADS>
+__device__ void lsweep_adj_reg(T *buf, int nn, int lw, int ie = 0) {
     const int tid = threadIdx.x;
     const uint32_t nel = (2u << nn) << lw;
     const uint32_t cmask = (1u << lw) - 1u;
     T own[R];
 #pragma unroll
     for (int j = 0; j < R; j++) {
-        uint32_t e = tid + j * SW_THREADS;
+        uint32_t e = tid + j * NT;
         own[j] = (e < nel) ? buf[e] : (T)0;
     }
-    for (int i = nn - 1; i >= 0; i--) {
+    for (int i = nn - 1; i >= ie; i--) {
         const int m = nn - i - 1;
         const uint32_t row_lo = 2u << m;
         const uint32_t lomask = (1u << m) - 1u;
 #pragma unroll
         for (int j = 0; j < R; j++) {
-            uint32_t e = tid + j * SW_THREADS;
+            uint32_t e = tid + j * NT;
             uint32_t Q = e >> lw;
             if (e < nel && Q >= row_lo) {
                 uint32_t cq = ((Q >> (m + 1)) << m) | (Q & lomask);
@@ -105,7 +105,7 @@ __device__ void lsweep_adj_reg(T *buf, int nn, int lw) {
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < R; j++) {
-            uint32_t e = tid + j * SW_THREADS;
+            uint32_t e = tid + j * NT;
             if (e < nel && (e >> lw) >= row_lo) buf[e] = own[j];
         }
         __syncthreads();
@@ -144,23 +144,23 @@ __device__ __forceinline__ void ld2(const double *p, double *v) {
 }
 
 // forward, tile of >= 4 columns (lw >= 2): group g = 4 columns of row (4g) >> lw
-template <typename T, int G>
-__device__ void lsweep_fwd_cols4(T *buf, int nn, int lw) {
+template <typename T, int G, int NT = SW_THREADS>
+__device__ void lsweep_fwd_cols4(T *buf, int nn, int lw, int ib = 0) {
     const int tid = threadIdx.x;
     const uint32_t ng = ((1u << nn) << lw) >> 2;
     const uint32_t cmask = (1u << lw) - 1u;
     T own[G][4];
 #pragma unroll
     for (int j = 0; j < G; j++) {
-        uint32_t g = tid + j * SW_THREADS;
+        uint32_t g = tid + j * NT;
         if (g < ng) ld4(buf + 4 * g, own[j]);
     }
-    for (int i = 0; i < nn; i++) {
+    for (int i = ib; i < nn; i++) {
         const int m = nn - i - 1;
         const uint32_t row_lo = 1u << m;
 #pragma unroll
         for (int j = 0; j < G; j++) {
-            uint32_t g = tid + j * SW_THREADS;
+            uint32_t g = tid + j * NT;
             uint32_t e = 4 * g, P = e >> lw;
             if (g < ng && P >= row_lo) {
                 uint32_t c = e & cmask;
@@ -175,7 +175,7 @@ __device__ void lsweep_fwd_cols4(T *buf, int nn, int lw) {
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < G; j++) {
-            uint32_t g = tid + j * SW_THREADS;
+            uint32_t g = tid + j * NT;
             if (g < ng && ((4 * g) >> lw) >= row_lo) st4(buf + 4 * g, own[j]);
         }
         __syncthreads();
@@ -183,22 +183,22 @@ __device__ void lsweep_fwd_cols4(T *buf, int nn, int lw) {
 }
 
 // forward, one-column tile (lw == 0): group g = rows 4g..4g+3 (nn >= 2)
-template <typename T, int G>
-__device__ void lsweep_fwd_rows4(T *buf, int nn) {
+template <typename T, int G, int NT = SW_THREADS>
+__device__ void lsweep_fwd_rows4(T *buf, int nn, int ib = 0) {
     const int tid = threadIdx.x;
     const uint32_t ng = (1u << nn) >> 2;
     T own[G][4];
 #pragma unroll
     for (int j = 0; j < G; j++) {
-        uint32_t g = tid + j * SW_THREADS;
+        uint32_t g = tid + j * NT;
         if (g < ng) ld4(buf + 4 * g, own[j]);
     }
-    for (int i = 0; i < nn; i++) {
+    for (int i = ib; i < nn; i++) {
         const int m = nn - i - 1;
         const uint32_t row_lo = 1u << m;
 #pragma unroll
         for (int j = 0; j < G; j++) {
-            uint32_t g = tid + j * SW_THREADS;
+            uint32_t g = tid + j * NT;
             uint32_t P0 = 4 * g;
             if (g < ng && P0 + 3 >= row_lo) {
                 T v[8];
@@ -226,7 +226,7 @@ __device__ void lsweep_fwd_rows4(T *buf, int nn) {
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < G; j++) {
-            uint32_t g = tid + j * SW_THREADS;
+            uint32_t g = tid + j * NT;
             uint32_t P0 = 4 * g;
             if (g < ng && P0 + 3 >= row_lo) {
                 if (P0 >= row_lo) st4(buf + P0, own[j]);
@@ -240,24 +240,24 @@ __device__ void lsweep_fwd_rows4(T *buf, int nn) {
 }
 
 // adjoint, tile of >= 4 columns
-template <typename T, int G>
-__device__ void lsweep_adj_cols4(T *buf, int nn, int lw) {
+template <typename T, int G, int NT = SW_THREADS>
+__device__ void lsweep_adj_cols4(T *buf, int nn, int lw, int ie = 0) {
     const int tid = threadIdx.x;
     const uint32_t ng = ((2u << nn) << lw) >> 2;
     const uint32_t cmask = (1u << lw) - 1u;
     T own[G][4];
 #pragma unroll
     for (int j = 0; j < G; j++) {
-        uint32_t g = tid + j * SW_THREADS;
+        uint32_t g = tid + j * NT;
         if (g < ng) ld4(buf + 4 * g, own[j]);
     }
-    for (int i = nn - 1; i >= 0; i--) {
+    for (int i = nn - 1; i >= ie; i--) {
         const int m = nn - i - 1;
         const uint32_t row_lo = 2u << m;
         const uint32_t lomask = (1u << m) - 1u;
 #pragma unroll
         for (int j = 0; j < G; j++) {
-            uint32_t g = tid + j * SW_THREADS;
+            uint32_t g = tid + j * NT;
             uint32_t e = 4 * g, Q = e >> lw;
             if (g < ng && Q >= row_lo) {
                 uint32_t cq = ((Q >> (m + 1)) << m) | (Q & lomask);
@@ -270,7 +270,7 @@ __device__ void lsweep_adj_cols4(T *buf, int nn, int lw) {
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < G; j++) {
-            uint32_t g = tid + j * SW_THREADS;
+            uint32_t g = tid + j * NT;
             if (g < ng && ((4 * g) >> lw) >= row_lo) st4(buf + 4 * g, own[j]);
         }
         __syncthreads();
@@ -278,23 +278,23 @@ __device__ void lsweep_adj_cols4(T *buf, int nn, int lw) {
 }
 
 // adjoint, one-column tile (nn >= 1): group g = rows 4g..4g+3
-template <typename T, int G>
-__device__ void lsweep_adj_rows4(T *buf, int nn) {
+template <typename T, int G, int NT = SW_THREADS>
+__device__ void lsweep_adj_rows4(T *buf, int nn, int ie = 0) {
     const int tid = threadIdx.x;
     const uint32_t ng = (2u << nn) >> 2;
     T own[G][4];
 #pragma unroll
     for (int j = 0; j < G; j++) {
-        uint32_t g = tid + j * SW_THREADS;
+        uint32_t g = tid + j * NT;
         if (g < ng) ld4(buf + 4 * g, own[j]);
     }
-    for (int i = nn - 1; i >= 0; i--) {
+    for (int i = nn - 1; i >= ie; i--) {
         const int m = nn - i - 1;
         const uint32_t row_lo = 2u << m;
         const uint32_t lomask = (1u << m) - 1u;
 #pragma unroll
         for (int j = 0; j < G; j++) {
-            uint32_t g = tid + j * SW_THREADS;
+            uint32_t g = tid + j * NT;
             uint32_t Q0 = 4 * g;
             if (g < ng && Q0 + 3 >= row_lo) {
                 if (m >= 2) {
@@ -318,7 +318,7 @@ __device__ void lsweep_adj_rows4(T *buf, int nn) {
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < G; j++) {
-            uint32_t g = tid + j * SW_THREADS;
+            uint32_t g = tid + j * NT;
             uint32_t Q0 = 4 * g;
             if (g < ng && Q0 + 3 >= row_lo) {
                 if (Q0 >= row_lo) st4(buf + Q0, own[j]);
@@ -333,22 +333,64 @@ __device__ void lsweep_adj_rows4(T *buf, int nn) {
 
 // choose the form: R = elements per thread (power of two).  R >= 4 and a tile
 // of >= 4 columns or one column use the 4-wide forms; otherwise scalar.
-template <typename T, int R>
-__device__ __forceinline__ void lsweep_fwd_any(T *buf, int nn, int lw) {
+template <typename T, int R, int NT = SW_THREADS>
+__device__ __forceinline__ void lsweep_fwd_any(T *buf, int nn, int lw, int ib = 0) {
     if constexpr (R >= 4) {
-        if (lw >= 2) { lsweep_fwd_cols4<T, R / 4>(buf, nn, lw); return; }
-        if (lw == 0 && nn >= 2) { lsweep_fwd_rows4<T, R / 4>(buf, nn); return; }
+        if (lw >= 2) { lsweep_fwd_cols4<T, R / 4, NT>(buf, nn, lw, ib); return; }
+        if (lw == 0 && nn >= 2) { lsweep_fwd_rows4<T, R / 4, NT>(buf, nn, ib); return; }
     }
-    lsweep_fwd_reg<T, R>(buf, nn, lw);
+    lsweep_fwd_reg<T, R, NT>(buf, nn, lw, ib);
 }
 
-template <typename T, int R>
-__device__ __forceinline__ void lsweep_adj_any(T *buf, int nn, int lw) {
+template <typename T, int R, int NT = SW_THREADS>
+__device__ __forceinline__ void lsweep_adj_any(T *buf, int nn, int lw, int ie = 0) {
     if constexpr (R >= 4) {
-        if (lw >= 2) { lsweep_adj_cols4<T, R / 4>(buf, nn, lw); return; }
-        if (lw == 0 && nn >= 1) { lsweep_adj_rows4<T, R / 4>(buf, nn); return; }
+        if (lw >= 2) { lsweep_adj_cols4<T, R / 4, NT>(buf, nn, lw, ie); return; }
+        if (lw == 0 && nn >= 1) { lsweep_adj_rows4<T, R / 4, NT>(buf, nn, ie); return; }
     }
-    lsweep_adj_reg<T, R>(buf, nn, lw);
+    lsweep_adj_reg<T, R, NT>(buf, nn, lw, ie);
+}
+
+// ---------------------------------------------------------------------------
+// Register-resident steps.  Fix the last L input symbols of a tile (its low
+// L bits sigma, L = nn - NL).  The first NL forward steps consume the other
+// NL symbols and never change the low L bits of a row index: with
+// P = (P' << L) | sigma, the insert at position m >= L is the insert at
+// m - L on P', and the row ranges map the same way.  So one thread holding
+// the 2^NL inputs of its sigma runs those steps in registers, as a sweep
+// over a 2^(NL+1)-element tile of its own; likewise the last NL adjoint
+// steps.  Only the remaining L steps go through shared memory.
+// v[2^NL + r] is the input of row r (r in [0, 2^NL)), rows below start at 0.
+// ---------------------------------------------------------------------------
+template <typename T, int NL>
+__device__ __forceinline__ void local_fwd(T (&v)[2 << NL]) {
+#pragma unroll
+    for (int P = 0; P < (1 << NL); P++) v[P] = (T)0;
+#pragma unroll
+    for (int i = 0; i < NL; i++) {
+        const int m = NL - i - 1;
+        // increasing P: every read index is above P, so still the old level
+#pragma unroll
+        for (int P = 1 << m; P < (1 << NL); P++) {
+            const int i0 = ((P >> m) << (m + 1)) | (P & ((1 << m) - 1));
+            v[P] = v[P] + v[i0] + v[i0 | (1 << m)];
+        }
+    }
+}
+
+// the last NL adjoint steps; on return v[2^NL + r] holds row r's result
+template <typename T, int NL>
+__device__ __forceinline__ void local_adj(T (&v)[2 << NL]) {
+#pragma unroll
+    for (int i = NL - 1; i >= 0; i--) {
+        const int m = NL - i - 1;
+        // decreasing Q: every read index is below Q, so still the old level
+#pragma unroll
+        for (int Q = (2 << NL) - 1; Q >= (2 << m); Q--) {
+            const int cq = ((Q >> (m + 1)) << m) | (Q & ((1 << m) - 1));
+            v[Q] = v[Q] + v[cq];
+        }
+    }
 }
 
 // largest per-thread element count a tile can need (32K FP32 / 16K FP64 elements)
@@ -412,6 +454,14 @@ __device__ __forceinline__ double block_max(double v, double *red) {
     if (threadIdx.x == 0)
         for (int w = 0; w < SW_THREADS / 32; w++) s = fmax(s, red[w]);
     return s;
+}
+
+// CTAs per SM to plan registers for (512 threads each): as many tiles of
+// `bytes` as fit in shared memory, up to `most` (2 CTAs: 64 registers a
+// thread, 3: 40).  FP32 only: the FP64 epilogues need more registers.
+template <typename T>
+constexpr int tile_blocks(size_t bytes, int most) {
+    return sizeof(T) != 4 ? 1 : (int)std::min<size_t>((size_t)most, std::max<size_t>(1, (224 * 1024) / bytes));
 }
 
 // Complement half mode (p(x) = p(cpl x)): every sweep quantity is invariant
@@ -491,7 +541,7 @@ __device__ __forceinline__ void stage_rev_D(T *buf, const T *Dz, int n, int n1, 
 // p back.  With n2 == 0 the pass covers all n symbols and writes q, L.
 // ---------------------------------------------------------------------------
 template <typename T, int R, bool HALF>
-__global__ void __launch_bounds__(SW_THREADS) k_cols_fwd(SweepArgs a, T *p, const T *D, T *F1, T *q, T *L,
+__global__ void __launch_bounds__(SW_THREADS, tile_blocks<T>(2 * R * SW_THREADS * sizeof(T), 2)) k_cols_fwd(SweepArgs a, T *p, const T *D, T *F1, T *q, T *L,
                                                           int apply_update, int mode, int sym_rev) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *buf = reinterpret_cast<T *>(smem_raw);
@@ -518,7 +568,7 @@ __global__ void __launch_bounds__(SW_THREADS) k_cols_fwd(SweepArgs a, T *p, cons
     T psum = (T)0;  // per-thread partial in the working precision
     if (lw >= 2) {
         // 4 consecutive columns of one row per step: 16-byte global accesses
-#pragma unroll 4
+#pragma unroll 8
         for (uint32_t e = 4 * threadIdx.x; e < ntop; e += 4 * SW_THREADS) {
             uint32_t x1 = e >> lw, c = e & (w - 1u);
             size_t x = ((size_t)x1 << n2) | (col0 + c);
@@ -575,7 +625,7 @@ __global__ void __launch_bounds__(SW_THREADS) k_cols_fwd(SweepArgs a, T *p, cons
     if (n2 > 0) {
         T *Fz = F1 + z * a.strideN;
         if (lw >= 2) {
-#pragma unroll 4
+#pragma unroll 8
             for (uint32_t e = w + 4 * threadIdx.x; e < ntop; e += 4 * SW_THREADS) {
                 uint32_t row = e >> lw, c = e & (w - 1u);
                 T v[4];
@@ -602,7 +652,7 @@ __global__ void __launch_bounds__(SW_THREADS) k_cols_fwd(SweepArgs a, T *p, cons
 // pass 2 forward (rows): one row c1 per CTA; input row = F1[c1] (c1 < 2^n1)
 // or p[x1 = c1 - 2^n1]; output codes c2 < 32 go to the transposed Ts.
 template <typename T, int R, bool HALF>
-__global__ void __launch_bounds__(SW_THREADS) k_rows_fwd(SweepArgs a, const T *p, const T *F1, T *Tm, T *Ts) {
+__global__ void __launch_bounds__(SW_THREADS, tile_blocks<T>(2 * R * SW_THREADS * sizeof(T), R <= 8 ? 3 : 2)) k_rows_fwd(SweepArgs a, const T *p, const T *F1, T *Tm, T *Ts) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *buf = reinterpret_cast<T *>(smem_raw);
     const int z = blockIdx.y;
@@ -613,6 +663,7 @@ __global__ void __launch_bounds__(SW_THREADS) k_rows_fwd(SweepArgs a, const T *p
     const T *src = (c1 >= (1u << n1)) ? p + z * a.strideN + ((size_t)(c1 - (1u << n1)) << n2)
                                       : F1 + z * a.strideN + ((size_t)c1 << n2);
     if (!HALF) {
+#pragma unroll 8
         for (uint32_t e = threadIdx.x; e < half; e += SW_THREADS) {
             buf[half + e] = src[e];
             buf[e] = (T)0;
@@ -622,6 +673,7 @@ __global__ void __launch_bounds__(SW_THREADS) k_rows_fwd(SweepArgs a, const T *p
         const uint32_t cc = cpl_code(c1), hh = half >> 1, full2 = half - 1u;
         const T *srcm = (cc >= (1u << n1)) ? p + z * a.strideN + ((size_t)(cc - (1u << n1)) << n2)
                                            : F1 + z * a.strideN + ((size_t)cc << n2);
+#pragma unroll 8
         for (uint32_t e = threadIdx.x; e < half; e += SW_THREADS) {
             buf[half + e] = (e < hh) ? src[e] : srcm[full2 - e];
             buf[e] = (T)0;
@@ -673,11 +725,14 @@ __global__ void k_combine(SweepArgs a, const T *p, const T *F1, const T *Tm, con
         }
         T qv = acc * inv_binom_t<T>(a, k);
         T lv = log2_t<T>(mode == MODE_CERT ? fmin(qv, (T)1) : fmax(qv, q_floor_t<T>(a)));
-        qz[c] = qv;
+        // a BA iteration needs log2 q only, and in half mode only at the codes
+        // the adjoint rows pass gathers: H1 codes, and every code of length <= n2
+        const bool keep_q = mode != MODE_ITER;
+        if (keep_q) qz[c] = qv;
         Lz[c] = lv;
-        if (HALF && k > 0) {
+        if (HALF && k > 0 && (keep_q || k <= n2)) {
             const uint32_t cm = cpl_code(c);
-            qz[cm] = qv;
+            if (keep_q) qz[cm] = qv;
             Lz[cm] = lv;
         }
     }
@@ -686,7 +741,7 @@ __global__ void k_combine(SweepArgs a, const T *p, const T *F1, const T *Tm, con
 // pass 2 adjoint (rows): gather omega_k L(code c1 . c2) over the row, adjoint
 // sweep over x2, write the row's top half to Gb[c1][x2].
 template <typename T, int R, bool HALF>
-__global__ void __launch_bounds__(SW_THREADS) k_rows_adj(SweepArgs a, const T *Lsrc, const T *omega, T *Gb) {
+__global__ void __launch_bounds__(SW_THREADS, tile_blocks<T>(R * SW_THREADS * sizeof(T), R <= 16 ? 3 : 2)) k_rows_adj(SweepArgs a, const T *Lsrc, const T *omega, T *Gb) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *buf = reinterpret_cast<T *>(smem_raw);
     const int z = blockIdx.y;
@@ -696,6 +751,7 @@ __global__ void __launch_bounds__(SW_THREADS) k_rows_adj(SweepArgs a, const T *L
     const int j = bitlen32(c1) - 1;
     const T *Lz = Lsrc + z * a.strideM;
     const T *om = omega + z * (n + 1);
+#pragma unroll 8
     for (uint32_t c2 = threadIdx.x; c2 < (2u << n2); c2 += SW_THREADS) {
         T v = (T)0;
         if (c2 > 0) {
@@ -709,6 +765,7 @@ __global__ void __launch_bounds__(SW_THREADS) k_rows_adj(SweepArgs a, const T *L
     lsweep_adj_any<T, R>(buf, n2, 0);
     T *Gz = Gb + z * a.strideM + ((size_t)c1 << n2);
     const uint32_t half = 1u << n2;
+#pragma unroll 8
     for (uint32_t e = threadIdx.x; e < half; e += SW_THREADS) Gz[e] = buf[half + e];
     (void)n1;
 }
@@ -725,7 +782,7 @@ struct EpiArgs {
 // pass 1 adjoint (columns): load Gb (or omega L directly when n2 == 0), adjoint
 // sweep over x1, then the epilogue D_x = -Hb(x) - G(x) and block partials.
 template <typename T, int R, bool HALF>
-__global__ void __launch_bounds__(SW_THREADS) k_cols_adj(SweepArgs a, EpiArgs ep, const T *Gb, const T *Lsrc,
+__global__ void __launch_bounds__(SW_THREADS, tile_blocks<T>(R * SW_THREADS * sizeof(T), 2)) k_cols_adj(SweepArgs a, EpiArgs ep, const T *Gb, const T *Lsrc,
                                                           const T *omega, int mode) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *buf = reinterpret_cast<T *>(smem_raw);
@@ -742,7 +799,7 @@ __global__ void __launch_bounds__(SW_THREADS) k_cols_adj(SweepArgs a, EpiArgs ep
         const T *Gz = Gb + z * a.strideM;
         const uint32_t full2 = (1u << n2) - 1u;
         if (lw >= 2) {
-#pragma unroll 4
+#pragma unroll 16
             for (uint32_t e = 4 * threadIdx.x; e < nall; e += 4 * SW_THREADS) {
                 uint32_t row = e >> lw, c = e & (w - 1u);
                 T v[4] = {(T)0, (T)0, (T)0, (T)0};
@@ -788,7 +845,7 @@ __global__ void __launch_bounds__(SW_THREADS) k_cols_adj(SweepArgs a, EpiArgs ep
     const double add = (mode == MODE_DIV) ? inst[I_SUMP] : 0.0;
     if (mode == MODE_ITER && lw >= 2) {
         T *Dz = reinterpret_cast<T *>(ep.Dout) + z * a.strideN;
-#pragma unroll 2
+#pragma unroll 8
         for (uint32_t e = 4 * threadIdx.x; e < ntop; e += 4 * SW_THREADS) {
             uint32_t x1 = e >> lw, c = e & (w - 1u);
             size_t x = ((size_t)x1 << n2) | (col0 + c);
@@ -866,6 +923,234 @@ __global__ void __launch_bounds__(SW_THREADS) k_cols_adj(SweepArgs a, EpiArgs ep
     }
 }
 
+// ---------------------------------------------------------------------------
+// Split-schedule kernels with register-resident steps (BA iterations).  A
+// column tile has exactly SW_THREADS << NL inputs, and thread t owns
+// c = t mod w and sigma = t / w (the low L = n1 - NL bits of x1): it loads
+// its 2^NL inputs x1 = (r << L) | sigma straight into registers, runs the
+// first NL steps there, and hands the state to shared memory for the other
+// L steps (the adjoint runs the mirror image, and its epilogue reads the
+// results from registers).  A row tile (one column, 2^LT threads, L = LT)
+// is handled the same way.  Same arithmetic, in the same order, as the
+// all-shared-memory kernels.
+// ---------------------------------------------------------------------------
+
+template <typename T, int NL, bool HALF>
+__global__ void __launch_bounds__(SW_THREADS, tile_blocks<T>((size_t)SW_THREADS * (2 << NL) * sizeof(T), 2))
+k_cols_fwd_l(SweepArgs a, T *p, const T *D, T *F1, int apply_update,
+                                                            int sym_rev) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *buf = reinterpret_cast<T *>(smem_raw);
+    __shared__ T red[2 * SW_THREADS / 32];
+    constexpr int NI = 1 << NL;
+    const int z = blockIdx.y;
+    const double *inst = a.inst + z * INST_STRIDE;
+    if (!flag_set(inst, I_ACTIVE)) return;
+    const int n1 = a.n1, n2 = a.n2, lw = a.lw, L = n1 - NL;
+    const uint32_t w = 1u << lw, col0 = blockIdx.x << lw;
+    const uint32_t c = threadIdx.x & (w - 1u), sigma = threadIdx.x >> lw;
+    T *pz = p + z * a.strideN;
+    const T *Dz = D + z * a.strideN;
+    const bool upd = apply_update && flag_set(inst, I_PENDING);
+    const T shift = (T)inst[I_SHIFT];
+    const bool symr = HALF && sym_rev && upd && flag_set(inst, I_SYMNEED);
+    const int sb = swz_bits(n1, lw);
+    if (symr) {
+        stage_rev_D<T>(buf, Dz, a.n, n1, n2, lw, col0, sb);
+        __syncthreads();
+    }
+    T v[2 * NI];
+    T psum = (T)0;
+#pragma unroll
+    for (int r = 0; r < NI; r++) {
+        const uint32_t x1 = ((uint32_t)r << L) | sigma;
+        const size_t x = ((size_t)x1 << n2) | (col0 + c);
+        T pv = pz[x];
+        if (upd) {
+            T dv = Dz[x];
+            if (symr) dv = (dv + buf[swz_pos(x1, c, lw, n1, sb)]) * (T)0.5;
+            pv = pv * exp2_t<T>(dv - shift);
+            pz[x] = pv;
+        }
+        v[NI + r] = pv;
+        psum += pv;
+    }
+    if (symr) __syncthreads();  // every staged value is read: the rows are reused below
+    local_fwd<T, NL>(v);
+#pragma unroll
+    for (int r = 1; r < 2 * NI; r++) buf[((((uint32_t)r << L) | sigma) << lw) | c] = v[r];
+    buf[(sigma << lw) | c] = (T)0;  // rows [0, 2^L) start the shared-memory steps at 0
+    T pmax = (T)0;
+    block_sum_max_t<T>(psum, pmax, red);  // (its barrier also publishes the rows above)
+    if (threadIdx.x == 0) {
+        double *pp = a.part + ((size_t)z * 2 + 0) * a.maxblk * 4 + blockIdx.x * 4;
+        pp[0] = (double)psum * (HALF ? 2.0 : 1.0);  // each column also stands for its complement
+    }
+    lsweep_fwd_any<T, NI>(buf, n1, lw, NL);
+    T *Fz = F1 + z * a.strideN;
+    const uint32_t ntop = (1u << n1) << lw;
+    if (lw >= 2) {
+#pragma unroll 8
+        for (uint32_t e = w + 4 * threadIdx.x; e < ntop; e += 4 * SW_THREADS) {
+            uint32_t row = e >> lw, cc = e & (w - 1u);
+            T t4[4];
+            ld4(buf + e, t4);
+            st4(Fz + (((size_t)row << n2) | (col0 + cc)), t4);
+        }
+    } else {
+        for (uint32_t e = threadIdx.x + w; e < ntop; e += SW_THREADS) {
+            uint32_t row = e >> lw, cc = e & (w - 1u);
+            Fz[((size_t)row << n2) | (col0 + cc)] = buf[e];
+        }
+    }
+}
+
+template <typename T, int NL, bool HALF>
+__global__ void __launch_bounds__(SW_THREADS, tile_blocks<T>((size_t)SW_THREADS * (2 << NL) * sizeof(T), 2))
+k_cols_adj_l(SweepArgs a, EpiArgs ep, const T *Gb) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *buf = reinterpret_cast<T *>(smem_raw);
+    __shared__ T red[2 * SW_THREADS / 32];
+    constexpr int NI = 1 << NL;
+    const int z = blockIdx.y;
+    if (!flag_set(a.inst + z * INST_STRIDE, I_ACTIVE)) return;
+    const int n1 = a.n1, n2 = a.n2, lw = a.lw, L = n1 - NL;
+    const uint32_t w = 1u << lw, col0 = blockIdx.x << lw;
+    const uint32_t nall = (2u << n1) << lw;
+    const T *Gz = Gb + z * a.strideM;
+    const uint32_t full2 = (1u << n2) - 1u;
+    if (lw >= 2) {
+#pragma unroll 16
+        for (uint32_t e = 4 * threadIdx.x; e < nall; e += 4 * SW_THREADS) {
+            uint32_t row = e >> lw, cc = e & (w - 1u);
+            T t4[4] = {(T)0, (T)0, (T)0, (T)0};
+            if (row) {
+                if (!HALF || in_h1(row)) {
+                    ld4(Gz + (((size_t)row << n2) | (col0 + cc)), t4);
+                } else {
+                    // rows outside H1: complement row, complement columns (reversed)
+                    T t[4];
+                    ld4(Gz + (((size_t)cpl_code(row) << n2) | (full2 - (col0 + cc) - 3u)), t);
+                    t4[0] = t[3]; t4[1] = t[2]; t4[2] = t[1]; t4[3] = t[0];
+                }
+            }
+            st4(buf + e, t4);
+        }
+    } else {
+        for (uint32_t e = threadIdx.x; e < nall; e += SW_THREADS) {
+            uint32_t row = e >> lw, cc = e & (w - 1u);
+            T t = (T)0;
+            if (row) t = (!HALF || in_h1(row)) ? Gz[((size_t)row << n2) | (col0 + cc)]
+                                               : Gz[((size_t)cpl_code(row) << n2) | (full2 - (col0 + cc))];
+            buf[e] = t;
+        }
+    }
+    __syncthreads();
+    lsweep_adj_any<T, 2 * NI>(buf, n1, lw, NL);
+    const uint32_t c = threadIdx.x & (w - 1u), sigma = threadIdx.x >> lw;
+    T v[2 * NI];
+    v[0] = (T)0;
+#pragma unroll
+    for (int r = 1; r < 2 * NI; r++) v[r] = buf[((((uint32_t)r << L) | sigma) << lw) | c];
+    local_adj<T, NL>(v);
+    const T *Hbz = reinterpret_cast<const T *>(ep.Hb) + z * a.strideN;
+    const T *pz = reinterpret_cast<const T *>(ep.p) + z * a.strideN;
+    T *Dz = reinterpret_cast<T *>(ep.Dout) + z * a.strideN;
+    T tZ = (T)0, tM = (T)-INFINITY;
+#pragma unroll
+    for (int r = 0; r < NI; r++) {
+        const size_t x = ((size_t)(((uint32_t)r << L) | sigma) << n2) | (col0 + c);
+        const T Dv = -Hbz[x] - v[NI + r];
+        Dz[x] = Dv;
+        tZ += pz[x] * exp2_t<T>(Dv);
+        tM = Dv > tM ? Dv : tM;
+    }
+    block_sum_max_t<T>(tZ, tM, red);
+    if (threadIdx.x == 0) {
+        double *pp = a.part + ((size_t)z * 2 + 1) * a.maxblk * 4 + blockIdx.x * 4;
+        pp[0] = (double)tZ * (HALF ? 2.0 : 1.0);  // each column also stands for its complement
+        pp[1] = (double)tM;
+        pp[2] = 0.0;
+        pp[3] = -INFINITY;
+    }
+}
+
+// rows pass, one row c1 per CTA, 2^LT threads, thread = sigma (n2 = NL + LT)
+template <typename T, int NL, bool HALF, int LT>
+__global__ void __launch_bounds__(1 << LT) k_rows_fwd_l(SweepArgs a, const T *p, const T *F1, T *Tm, T *Ts) {
+    constexpr int ROW_THREADS = 1 << LT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *buf = reinterpret_cast<T *>(smem_raw);
+    constexpr int NI = 1 << NL;
+    const int z = blockIdx.y;
+    if (!flag_set(a.inst + z * INST_STRIDE, I_ACTIVE)) return;
+    const int n1 = a.n1, n2 = a.n2, L = n2 - NL;
+    const uint32_t c1 = HALF ? half_row(blockIdx.x) : blockIdx.x + 1;
+    const uint32_t half = 1u << n2, sigma = threadIdx.x;
+    const T *src = (c1 >= (1u << n1)) ? p + z * a.strideN + ((size_t)(c1 - (1u << n1)) << n2)
+                                      : F1 + z * a.strideN + ((size_t)c1 << n2);
+    const T *srcm = src;
+    if (HALF) {
+        // columns x2 >= 2^(n2-1) of row c1 are the complement row at column cpl(x2)
+        const uint32_t cc = cpl_code(c1);
+        srcm = (cc >= (1u << n1)) ? p + z * a.strideN + ((size_t)(cc - (1u << n1)) << n2)
+                                  : F1 + z * a.strideN + ((size_t)cc << n2);
+    }
+    T v[2 * NI];
+#pragma unroll
+    for (int r = 0; r < NI; r++) {
+        const uint32_t x2 = ((uint32_t)r << L) | sigma;
+        v[NI + r] = (HALF && x2 >= (half >> 1)) ? srcm[half - 1u - x2] : src[x2];
+    }
+    local_fwd<T, NL>(v);
+#pragma unroll
+    for (int r = 1; r < 2 * NI; r++) buf[((uint32_t)r << L) | sigma] = v[r];
+    buf[sigma] = (T)0;
+    __syncthreads();
+    lsweep_fwd_any<T, NI, ROW_THREADS>(buf, n2, 0, NL);
+    T *Tmz = Tm + z * a.strideM;
+    T *Tsz = Ts + z * ((size_t)32 << (n1 + 1));
+    for (uint32_t c2 = threadIdx.x + 1; c2 < half; c2 += ROW_THREADS) {
+        if (c2 < 32) Tsz[((size_t)c2 << (n1 + 1)) + c1] = buf[c2];
+        else Tmz[((size_t)c1 << n2) + c2] = buf[c2];
+    }
+}
+
+template <typename T, int NL, bool HALF, int LT>
+__global__ void __launch_bounds__(1 << LT) k_rows_adj_l(SweepArgs a, const T *Lsrc, const T *omega, T *Gb) {
+    constexpr int ROW_THREADS = 1 << LT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *buf = reinterpret_cast<T *>(smem_raw);
+    constexpr int NI = 1 << NL;
+    const int z = blockIdx.y;
+    if (!flag_set(a.inst + z * INST_STRIDE, I_ACTIVE)) return;
+    const int n2 = a.n2, n = a.n, L = n2 - NL;
+    const uint32_t c1 = HALF ? half_row(blockIdx.x) : blockIdx.x + 1;
+    const int j = bitlen32(c1) - 1;
+    const T *Lz = Lsrc + z * a.strideM;
+    const T *om = omega + z * (n + 1);
+    for (uint32_t c2 = threadIdx.x; c2 < (2u << n2); c2 += ROW_THREADS) {
+        T t = (T)0;
+        if (c2 > 0) {
+            int l = bitlen32(c2) - 1;
+            uint32_t code = (c1 << l) | (c2 ^ (1u << l));
+            t = om[j + l] * Lz[code];
+        }
+        buf[c2] = t;
+    }
+    __syncthreads();
+    lsweep_adj_any<T, 2 * NI, ROW_THREADS>(buf, n2, 0, NL);
+    const uint32_t sigma = threadIdx.x;
+    T v[2 * NI];
+    v[0] = (T)0;
+#pragma unroll
+    for (int r = 1; r < 2 * NI; r++) v[r] = buf[((uint32_t)r << L) | sigma];
+    local_adj<T, NL>(v);
+    T *Gz = Gb + z * a.strideM + ((size_t)c1 << n2);
+#pragma unroll
+    for (int r = 0; r < NI; r++) Gz[((uint32_t)r << L) | sigma] = v[NI + r];
+}
+
 template <typename T>
 SweepArgs make_args(bdc_engine *e, PrecBuf<T> &b) {
     SweepArgs a{};
@@ -924,6 +1209,27 @@ inline int r_of(size_t elems) {
         }                                                                                     \
     } while (0)
 
+// run BODY with the compile-time constant NL equal to the runtime value nl
+// (3 <= nl <= 5; 5 only for FP32 tiles)
+#define SW_WITH_NL(T, nl, BODY)                                                  \
+    do {                                                                        \
+        switch (nl) {                                                           \
+            case 3: { constexpr int NL = 3; BODY; } break;                      \
+            case 4: { constexpr int NL = 4; BODY; } break;                      \
+            default: { constexpr int NL = (sizeof(T) == 4 ? 5 : 4); BODY; } break; \
+        }                                                                       \
+    } while (0)
+
+// run BODY with the compile-time constant LT equal to the runtime value lt (7..9)
+#define SW_WITH_LT(lt, BODY)                                \
+    do {                                                    \
+        switch (lt) {                                       \
+            case 7: { constexpr int LT = 7; BODY; } break;  \
+            case 8: { constexpr int LT = 8; BODY; } break;  \
+            default: { constexpr int LT = 9; BODY; } break; \
+        }                                                   \
+    } while (0)
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -954,6 +1260,8 @@ Sched make_sched(int n, int elem_bytes, int n2_override, int w_override) {
     if (w_override) {
         lw = 0;
         while ((1 << (lw + 1)) <= w_override) lw++;
+        // clamp to a tile that fits and to at most the 2^n2 columns
+        while (lw > 0 && (((size_t)2 << s.n1 << lw) > (size_t)tile || lw > n2)) lw--;
     }
     s.lw = lw;
     s.nblk_cols = 1 << (n2 - lw);
@@ -974,6 +1282,18 @@ cudaError_t prepare_all(size_t cols_bytes, size_t rows_bytes) {
     }
 #define PREP_ONE(RR) PREP_ONE_H(RR, false) PREP_ONE_H(RR, true)
     PREP_ONE(1) PREP_ONE(2) PREP_ONE(4) PREP_ONE(8) PREP_ONE(16) PREP_ONE(32) PREP_ONE(64)
+#define PREP_L(NL, H)                                                                        \
+    if (err == cudaSuccess) err = allow_smem(k_cols_fwd_l<T, NL, H>, cols_bytes);            \
+    if (err == cudaSuccess) err = allow_smem(k_cols_adj_l<T, NL, H>, cols_bytes);            \
+    if (err == cudaSuccess) err = allow_smem(k_rows_adj_l<T, NL, H, 9>, rows_bytes);
+    PREP_L(3, false) PREP_L(3, true) PREP_L(4, false) PREP_L(4, true)
+    if constexpr (sizeof(T) == 4) { PREP_L(5, false) PREP_L(5, true) }
+#undef PREP_L
+    constexpr int NLR = sizeof(T) == 4 ? 5 : 4;
+#define PREP_R(LT, H) \
+    if (err == cudaSuccess) err = allow_smem(k_rows_fwd_l<T, NLR, H, LT>, rows_bytes);
+    PREP_R(7, false) PREP_R(7, true) PREP_R(8, false) PREP_R(8, true) PREP_R(9, false) PREP_R(9, true)
+#undef PREP_R
 #undef PREP_ONE
 #undef PREP_ONE_H
     return err;
@@ -990,6 +1310,27 @@ bdc_status sweep_prepare(bdc_engine *e, PrecBuf<T> &b) {
 
 bool half_possible(const Sched &s) { return s.n2 > 0 && s.lw < s.n2 && s.n1 >= 1; }
 
+// register-resident steps (bits of opt.use_regsteps: 1 forward rows,
+// 2 adjoint rows, 4 forward columns, 8 adjoint columns): NL of a tile, 0
+// where they are off or do not apply.  A column tile must hold
+// SW_THREADS << NL inputs; a forward row tile runs NL = 5 (FP32) / 4 (FP64)
+// on 2^(n2 - NL) threads, an adjoint row tile NL = n2 - 9 on 512 threads.
+template <typename T>
+static int nl_cols(const bdc_engine *e, const Sched &s, int bit) {
+    const int nl = s.n1 + s.lw - 9, nmax = sizeof(T) == 4 ? 5 : 4;
+    return ((e->opt.use_regsteps & bit) && s.n2 > 0 && nl >= 3 && nl <= nmax && nl <= s.n1) ? nl : 0;
+}
+template <typename T>
+static int nl_rows_fwd(const bdc_engine *e, const Sched &s) {
+    const int nl = sizeof(T) == 4 ? 5 : 4, lt = s.n2 - nl;
+    return ((e->opt.use_regsteps & 1) && s.n2 > 0 && lt >= 7 && lt <= 9) ? nl : 0;
+}
+template <typename T>
+static int nl_rows_adj(const bdc_engine *e, const Sched &s) {
+    const int nl = s.n2 - 9, nmax = sizeof(T) == 4 ? 5 : 4;
+    return ((e->opt.use_regsteps & 2) && s.n2 > 0 && nl >= 3 && nl <= nmax) ? nl : 0;
+}
+
 template <typename T>
 bdc_status sweep_forward(bdc_engine *e, PrecBuf<T> &b, const T *p_src, int apply_update, int mode, bool half,
                          bool sym_rev) {
@@ -1000,7 +1341,14 @@ bdc_status sweep_forward(bdc_engine *e, PrecBuf<T> &b, const T *p_src, int apply
     T *p = const_cast<T *>(p_src);
     dim3 g1(half ? s.nblk_cols / 2 : s.nblk_cols, e->nd);
     const int rc = r_of(((size_t)1 << s.n1) << s.lw);
-    if (half)
+    const int nlc = (mode == MODE_ITER) ? nl_cols<T>(e, s, 4) : 0;
+    if (nlc && half)
+        SW_WITH_NL(T, nlc, (k_cols_fwd_l<T, NL, true><<<g1, SW_THREADS, sm1, e->stream>>>(
+                               a, p, b.D, b.F1, apply_update, sym_rev ? 1 : 0)));
+    else if (nlc)
+        SW_WITH_NL(T, nlc, (k_cols_fwd_l<T, NL, false><<<g1, SW_THREADS, sm1, e->stream>>>(
+                               a, p, b.D, b.F1, apply_update, 0)));
+    else if (half)
         SW_WITH_R(rmax_fwd<T>(), rc, (k_cols_fwd<T, R, true><<<g1, SW_THREADS, sm1, e->stream>>>(
                                          a, p, b.D, b.F1, b.q, b.L, apply_update, mode, sym_rev ? 1 : 0)));
     else
@@ -1012,7 +1360,13 @@ bdc_status sweep_forward(bdc_engine *e, PrecBuf<T> &b, const T *p_src, int apply
         size_t sm2 = tile_bytes_rows<T>(s);
         dim3 g2(half ? (1u << s.n1) : (2u << s.n1) - 1u, e->nd);
         const int rr = r_of((size_t)1 << s.n2);
-        if (half)
+        const int nlr = nl_rows_fwd<T>(e, s);
+        constexpr int NLR = sizeof(T) == 4 ? 5 : 4;
+        if (nlr && half)
+            SW_WITH_LT(s.n2 - nlr, (k_rows_fwd_l<T, NLR, true, LT><<<g2, 1 << LT, sm2, e->stream>>>(a, p, b.F1, b.Tm, b.Ts)));
+        else if (nlr)
+            SW_WITH_LT(s.n2 - nlr, (k_rows_fwd_l<T, NLR, false, LT><<<g2, 1 << LT, sm2, e->stream>>>(a, p, b.F1, b.Tm, b.Ts)));
+        else if (half)
             SW_WITH_R(rmax_fwd<T>(), rr,
                       (k_rows_fwd<T, R, true><<<g2, SW_THREADS, sm2, e->stream>>>(a, p, b.F1, b.Tm, b.Ts)));
         else
@@ -1040,7 +1394,12 @@ bdc_status sweep_adjoint(bdc_engine *e, PrecBuf<T> &b, const T *Lsrc, const T *o
         size_t sm2 = tile_bytes_rows<T>(s);
         dim3 g2(half ? (1u << s.n1) : (2u << s.n1) - 1u, e->nd);
         const int rr = r_of((size_t)2 << s.n2);
-        if (half)
+        const int nlr = nl_rows_adj<T>(e, s);
+        if (nlr && half)
+            SW_WITH_NL(T, nlr, (k_rows_adj_l<T, NL, true, 9><<<g2, SW_THREADS, sm2, e->stream>>>(a, Lsrc, omega, b.Gb)));
+        else if (nlr)
+            SW_WITH_NL(T, nlr, (k_rows_adj_l<T, NL, false, 9><<<g2, SW_THREADS, sm2, e->stream>>>(a, Lsrc, omega, b.Gb)));
+        else if (half)
             SW_WITH_R(rmax_adj<T>(), rr,
                       (k_rows_adj<T, R, true><<<g2, SW_THREADS, sm2, e->stream>>>(a, Lsrc, omega, b.Gb)));
         else
@@ -1063,7 +1422,12 @@ bdc_status sweep_adjoint(bdc_engine *e, PrecBuf<T> &b, const T *Lsrc, const T *o
     size_t sm1 = tile_bytes_cols<T>(s);
     dim3 g1(half ? s.nblk_cols / 2 : s.nblk_cols, e->nd);
     const int rc = r_of(((size_t)2 << s.n1) << s.lw);
-    if (half)
+    const int nlc = (mode == MODE_ITER) ? nl_cols<T>(e, s, 8) : 0;
+    if (nlc && half)
+        SW_WITH_NL(T, nlc, (k_cols_adj_l<T, NL, true><<<g1, SW_THREADS, sm1, e->stream>>>(a, ep, b.Gb)));
+    else if (nlc)
+        SW_WITH_NL(T, nlc, (k_cols_adj_l<T, NL, false><<<g1, SW_THREADS, sm1, e->stream>>>(a, ep, b.Gb)));
+    else if (half)
         SW_WITH_R(rmax_adj<T>(), rc,
                   (k_cols_adj<T, R, true><<<g1, SW_THREADS, sm1, e->stream>>>(a, ep, b.Gb, Lsrc, omega, mode)));
     else

@@ -230,3 +230,62 @@ def test_half_mode_keeps_p_exactly_orbit_invariant(prec):
     assert np.all(np.abs(la - lb) <= htol) and np.all(np.abs(ua - ub) <= htol)
     a.close()
     b.close()
+
+
+def _nl(sched, prec):
+    # which kernels run register-resident steps (use_regsteps = 15): columns
+    # when a column tile holds 512 << NL inputs (3 <= NL <= 5 in FP32, 4 in
+    # FP64); forward rows when n2 - NLmax is in [7, 9]; adjoint rows when
+    # 3 <= n2 - 9 <= NLmax
+    nmax = 5 if prec == "fp32" else 4
+    w = sched["width"].bit_length() - 1
+    nlc = sched["n1"] + w - 9
+    return {"cols": 3 <= nlc <= nmax and nlc <= sched["n1"], "rows_fwd": 7 <= sched["n2"] - nmax <= 9,
+            "rows_adj": 3 <= sched["n2"] - 9 <= nmax}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_register_steps_agree_with_shared_memory_steps(prec):
+    import paper_2604_05867_b300 as bdc
+    n, T = 20, 6
+    kw = dict(sched_n2_fp32=12, sched_w_fp32=32, sched_n2_fp64=12, sched_w_fp64=32)
+    a = bdc.Engine(n, [0.3, 0.7], options=bdc.default_options(use_regsteps=15, **kw))
+    b = bdc.Engine(n, [0.3, 0.7], options=bdc.default_options(use_regsteps=0, **kw))
+    assert all(_nl(a.schedule(prec), prec).values())
+    a.iterate(T, -1.0, prec, "sweep")
+    b.iterate(T, -1.0, prec, "sweep")
+    tol = 1e-12 if prec == "fp64" else 2e-6
+    for z in range(2):
+        la, ua = a.history(z)
+        lb, ub = b.history(z)
+        assert np.all(np.abs(la - lb) <= tol * np.abs(lb)) and np.all(np.abs(ua - ub) <= tol * np.abs(ub))
+    pa, pb = a.get_p(), b.get_p()
+    assert np.all(np.abs(pa - pb) <= (1e-11 if prec == "fp64" else 1e-4) * pb)
+    a.close()
+    b.close()
+
+
+def test_register_steps_match_oracle():
+    # n = 17 with a forced split (n1 = 7, n2 = 10, 32 columns): the column
+    # kernels run register-resident steps, in the complement half mode with
+    # the fused orbit mean (second iteration); the row kernels are covered in
+    # the sweep tests
+    import paper_2604_05867_b300 as bdc
+    n, d, T = 17, 0.6, 2
+    eng = bdc.Engine(n, [d], options=bdc.default_options(sched_n2_fp64=10, sched_w_fp64=32, use_regsteps=15))
+    assert _nl(eng.schedule("fp64"), "fp64")["cols"]
+    eng.iterate(T, -1.0, "fp64", "sweep")
+    # oracle BA from its matrix-free q and D (the sparse-row BA is too large here)
+    pr = np.full(1 << n, 1.0 / (1 << n))
+    lo_ref, up_ref = [], []
+    for _ in range(T):
+        D = oracle.D_full(n, d, oracle.q_full(n, d, pr))
+        lo_ref.append(np.log2(np.sum(pr * np.exp2(D))))
+        up_ref.append(D.max())
+        pr = pr * np.exp2(D)
+        pr /= pr.sum()
+    lo, up = eng.history(0)
+    assert np.all(np.abs(lo - lo_ref) <= 1e-11) and np.all(np.abs(up - up_ref) <= 1e-11)
+    p = eng.get_p()[0]
+    assert np.all(np.abs(p - pr) <= 1e-9 * pr)
+    eng.close()

@@ -86,6 +86,29 @@ def test_sampled_points_large(n, d):
     eng.close()
 
 
+@pytest.mark.parametrize("prec,tq,tD", [("fp64", 1e-12, 1e-11), ("fp32", 4e-6, 2e-5)])
+def test_sampled_points_register_steps(prec, tq, tD):
+    # n = 18 split as n1 = 6, n2 = 12: both row kernels run register-resident
+    # steps (forward: 2^5 or 2^4 inputs a thread; adjoint: the last 3 steps)
+    n, d = 18, 0.45
+    p = inputs.orbit_invariant_dirichlet(n, seed=5)
+    eng = _engine(n, [d], enable_literal=0, use_regsteps=15, sched_n2_fp32=12, sched_w_fp32=32,
+                  sched_n2_fp64=12, sched_w_fp64=32)
+    s = eng.schedule(prec)
+    assert (s["n1"], s["n2"]) == (6, 12)
+    eng.set_p(p)
+    q = eng.get_q(prec)[0]
+    for c in inputs.random_codes(n, 12, seed=6):
+        ref = oracle.q_point(n, d, p[0], int(c))
+        assert abs(q[c] - ref) <= tq * ref
+    D = eng.divergence(precision=prec).cpu().numpy()[0]
+    q64 = eng.get_q("fp64")[0]
+    for x in inputs.random_inputs(n, 12, seed=7):
+        ref = oracle.D_point(n, d, q64, int(x))
+        assert abs(D[x] - ref) <= tD * max(1.0, abs(ref))
+    eng.close()
+
+
 def test_batched_instances_are_independent():
     n = 10
     ds = [0.0, 0.2, 0.5, 0.95, 1.0]
