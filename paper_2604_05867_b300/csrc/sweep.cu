@@ -526,7 +526,7 @@ __device__ __forceinline__ void stage_rev_D(T *buf, const T *Dz, int n, int n1, 
                                             int sb) {
     const uint32_t ntop = (1u << n1) << lw, cm = (1u << lw) - 1u;
     const uint32_t full = (1u << n) - 1u;
-#pragma unroll 8
+#pragma unroll 4
     for (uint32_t idx = threadIdx.x; idx < ntop; idx += SW_THREADS) {
         const uint32_t o = idx >> lw, c = idx & cm;
         uint32_t j = (rev_bits(col0 + c, n2) << n1) | o;
@@ -691,7 +691,8 @@ __global__ void __launch_bounds__(SW_THREADS, tile_blocks<T>(2 * R * SW_THREADS 
 
 // combine: F_n(y) = sum over splits of the two passes' outputs; q_k = F_n / C(n,k)
 template <typename T, bool HALF>
-__global__ void k_combine(SweepArgs a, const T *p, const T *F1, const T *Tm, const T *Ts, T *q, T *L, int mode) {
+__global__ void k_combine(SweepArgs a, const T *__restrict__ p, const T *__restrict__ F1, const T *__restrict__ Tm,
+                          const T *__restrict__ Ts, T *__restrict__ q, T *__restrict__ L, int mode) {
     const int z = blockIdx.y;
     if (!flag_set(a.inst + z * INST_STRIDE, I_ACTIVE)) return;
     const int n1 = a.n1, n2 = a.n2, n = a.n;
@@ -738,6 +739,35 @@ __global__ void k_combine(SweepArgs a, const T *p, const T *F1, const T *Tm, con
     }
 }
 
+// adjoint rows input: buf[c2] = omega_{j+l} L(c1 . u2) for c2 = 2^l + u2
+// (l = |u2|, j = |c1|), buf[0] = 0.  For each length l the codes
+// (c1 << l) + u2 are 2^l contiguous values: 16-byte loads and stores from l = 2.
+template <typename T, int NT>
+__device__ __forceinline__ void gather_row_L(T *buf, const T *__restrict__ Lz, const T *__restrict__ om, uint32_t c1,
+                                             int j, int n2) {
+    if (threadIdx.x < 4) {
+        const uint32_t c2 = threadIdx.x;
+        T t = (T)0;
+        if (c2 > 0) {
+            const int l = bitlen32(c2) - 1;
+            t = om[j + l] * Lz[(c1 << l) | (c2 ^ (1u << l))];
+        }
+        buf[c2] = t;
+    }
+    for (int l = 2; l <= n2; l++) {
+        const T wl = om[j + l];
+        const T *src = Lz + ((size_t)c1 << l);
+        T *dst = buf + (1u << l);
+        for (uint32_t t = 4 * threadIdx.x; t < (1u << l); t += 4 * NT) {
+            T a4[4];
+            ld4(src + t, a4);
+#pragma unroll
+            for (int k = 0; k < 4; k++) a4[k] = wl * a4[k];
+            st4(dst + t, a4);
+        }
+    }
+}
+
 // pass 2 adjoint (rows): gather omega_k L(code c1 . c2) over the row, adjoint
 // sweep over x2, write the row's top half to Gb[c1][x2].
 template <typename T, int R, bool HALF>
@@ -749,18 +779,7 @@ __global__ void __launch_bounds__(SW_THREADS, tile_blocks<T>(R * SW_THREADS * si
     const int n1 = a.n1, n2 = a.n2, n = a.n;
     const uint32_t c1 = HALF ? half_row(blockIdx.x) : blockIdx.x + 1;
     const int j = bitlen32(c1) - 1;
-    const T *Lz = Lsrc + z * a.strideM;
-    const T *om = omega + z * (n + 1);
-#pragma unroll 8
-    for (uint32_t c2 = threadIdx.x; c2 < (2u << n2); c2 += SW_THREADS) {
-        T v = (T)0;
-        if (c2 > 0) {
-            int l = bitlen32(c2) - 1;
-            uint32_t code = (c1 << l) | (c2 ^ (1u << l));
-            v = om[j + l] * Lz[code];
-        }
-        buf[c2] = v;
-    }
+    gather_row_L<T, SW_THREADS>(buf, Lsrc + z * a.strideM, omega + z * (n + 1), c1, j, n2);
     __syncthreads();
     lsweep_adj_any<T, R>(buf, n2, 0);
     T *Gz = Gb + z * a.strideM + ((size_t)c1 << n2);
@@ -937,8 +956,8 @@ __global__ void __launch_bounds__(SW_THREADS, tile_blocks<T>(R * SW_THREADS * si
 
 template <typename T, int NL, bool HALF>
 __global__ void __launch_bounds__(SW_THREADS, tile_blocks<T>((size_t)SW_THREADS * (2 << NL) * sizeof(T), 2))
-k_cols_fwd_l(SweepArgs a, T *p, const T *D, T *F1, int apply_update,
-                                                            int sym_rev) {
+k_cols_fwd_l(SweepArgs a, T *__restrict__ p, const T *__restrict__ D, T *__restrict__ F1, int apply_update,
+             int sym_rev) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *buf = reinterpret_cast<T *>(smem_raw);
     __shared__ T red[2 * SW_THREADS / 32];
@@ -959,22 +978,29 @@ k_cols_fwd_l(SweepArgs a, T *p, const T *D, T *F1, int apply_update,
         stage_rev_D<T>(buf, Dz, a.n, n1, n2, lw, col0, sb);
         __syncthreads();
     }
+    // all of a thread's global loads are issued before its first store; input
+    // r of this thread sits at x0 + r * xs
+    const size_t x0 = ((size_t)sigma << n2) | (col0 + c), xs = (size_t)1 << (L + n2);
     T v[2 * NI];
+#pragma unroll
+    for (int r = 0; r < NI; r++) v[NI + r] = pz[x0 + r * xs];
+    if (upd) {
+        // D goes to the bottom half of v, free until the local steps
+#pragma unroll
+        for (int r = 0; r < NI; r++) v[r] = Dz[x0 + r * xs];
+#pragma unroll
+        for (int r = 0; r < NI; r++) {
+            const uint32_t x1 = ((uint32_t)r << L) | sigma;
+            T d = v[r];
+            if (symr) d = (d + buf[swz_pos(x1, c, lw, n1, sb)]) * (T)0.5;
+            v[NI + r] = v[NI + r] * exp2_t<T>(d - shift);
+        }
+#pragma unroll
+        for (int r = 0; r < NI; r++) pz[x0 + r * xs] = v[NI + r];
+    }
     T psum = (T)0;
 #pragma unroll
-    for (int r = 0; r < NI; r++) {
-        const uint32_t x1 = ((uint32_t)r << L) | sigma;
-        const size_t x = ((size_t)x1 << n2) | (col0 + c);
-        T pv = pz[x];
-        if (upd) {
-            T dv = Dz[x];
-            if (symr) dv = (dv + buf[swz_pos(x1, c, lw, n1, sb)]) * (T)0.5;
-            pv = pv * exp2_t<T>(dv - shift);
-            pz[x] = pv;
-        }
-        v[NI + r] = pv;
-        psum += pv;
-    }
+    for (int r = 0; r < NI; r++) psum += v[NI + r];
     if (symr) __syncthreads();  // every staged value is read: the rows are reused below
     local_fwd<T, NL>(v);
 #pragma unroll
@@ -990,7 +1016,7 @@ k_cols_fwd_l(SweepArgs a, T *p, const T *D, T *F1, int apply_update,
     T *Fz = F1 + z * a.strideN;
     const uint32_t ntop = (1u << n1) << lw;
     if (lw >= 2) {
-#pragma unroll 8
+#pragma unroll 4
         for (uint32_t e = w + 4 * threadIdx.x; e < ntop; e += 4 * SW_THREADS) {
             uint32_t row = e >> lw, cc = e & (w - 1u);
             T t4[4];
@@ -1007,7 +1033,7 @@ k_cols_fwd_l(SweepArgs a, T *p, const T *D, T *F1, int apply_update,
 
 template <typename T, int NL, bool HALF>
 __global__ void __launch_bounds__(SW_THREADS, tile_blocks<T>((size_t)SW_THREADS * (2 << NL) * sizeof(T), 2))
-k_cols_adj_l(SweepArgs a, EpiArgs ep, const T *Gb) {
+k_cols_adj_l(SweepArgs a, EpiArgs ep, const T *__restrict__ Gb) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *buf = reinterpret_cast<T *>(smem_raw);
     __shared__ T red[2 * SW_THREADS / 32];
@@ -1053,18 +1079,28 @@ k_cols_adj_l(SweepArgs a, EpiArgs ep, const T *Gb) {
 #pragma unroll
     for (int r = 1; r < 2 * NI; r++) v[r] = buf[((((uint32_t)r << L) | sigma) << lw) | c];
     local_adj<T, NL>(v);
-    const T *Hbz = reinterpret_cast<const T *>(ep.Hb) + z * a.strideN;
-    const T *pz = reinterpret_cast<const T *>(ep.p) + z * a.strideN;
-    T *Dz = reinterpret_cast<T *>(ep.Dout) + z * a.strideN;
+    const T *__restrict__ Hbz = reinterpret_cast<const T *>(ep.Hb) + z * a.strideN;
+    const T *__restrict__ pz = reinterpret_cast<const T *>(ep.p) + z * a.strideN;
+    T *__restrict__ Dz = reinterpret_cast<T *>(ep.Dout) + z * a.strideN;
+    // all of a thread's global loads are issued before its first store, in two
+    // rounds that fit the registers: Hb into the rows below 2^NL of v (dead
+    // after the local steps), D = -Hb - G there, then p over the G rows
+    const size_t x0 = ((size_t)sigma << n2) | (col0 + c), xs = (size_t)1 << (L + n2);
+#pragma unroll
+    for (int r = 0; r < NI; r++) v[r] = Hbz[x0 + r * xs];
+#pragma unroll
+    for (int r = 0; r < NI; r++) v[r] = -v[r] - v[NI + r];
+#pragma unroll
+    for (int r = 0; r < NI; r++) v[NI + r] = pz[x0 + r * xs];
     T tZ = (T)0, tM = (T)-INFINITY;
 #pragma unroll
     for (int r = 0; r < NI; r++) {
-        const size_t x = ((size_t)(((uint32_t)r << L) | sigma) << n2) | (col0 + c);
-        const T Dv = -Hbz[x] - v[NI + r];
-        Dz[x] = Dv;
-        tZ += pz[x] * exp2_t<T>(Dv);
+        const T Dv = v[r];
+        tZ += v[NI + r] * exp2_t<T>(Dv);
         tM = Dv > tM ? Dv : tM;
     }
+#pragma unroll
+    for (int r = 0; r < NI; r++) Dz[x0 + r * xs] = v[r];
     block_sum_max_t<T>(tZ, tM, red);
     if (threadIdx.x == 0) {
         double *pp = a.part + ((size_t)z * 2 + 1) * a.maxblk * 4 + blockIdx.x * 4;
@@ -1127,17 +1163,7 @@ __global__ void __launch_bounds__(1 << LT) k_rows_adj_l(SweepArgs a, const T *Ls
     const int n2 = a.n2, n = a.n, L = n2 - NL;
     const uint32_t c1 = HALF ? half_row(blockIdx.x) : blockIdx.x + 1;
     const int j = bitlen32(c1) - 1;
-    const T *Lz = Lsrc + z * a.strideM;
-    const T *om = omega + z * (n + 1);
-    for (uint32_t c2 = threadIdx.x; c2 < (2u << n2); c2 += ROW_THREADS) {
-        T t = (T)0;
-        if (c2 > 0) {
-            int l = bitlen32(c2) - 1;
-            uint32_t code = (c1 << l) | (c2 ^ (1u << l));
-            t = om[j + l] * Lz[code];
-        }
-        buf[c2] = t;
-    }
+    gather_row_L<T, ROW_THREADS>(buf, Lsrc + z * a.strideM, omega + z * (n + 1), c1, j, n2);
     __syncthreads();
     lsweep_adj_any<T, 2 * NI, ROW_THREADS>(buf, n2, 0, NL);
     const uint32_t sigma = threadIdx.x;
