@@ -219,8 +219,10 @@ def run_ours(args, rank: int, world: int):
         sched32 = eng.autotune("fp32", reps=3, cache=args.sched_cache)
         sched64 = eng.autotune("fp64", reps=2, cache=args.sched_cache)
 
-        # warm-up: W untimed FP32 iterations
+        # warm-up: W untimed FP32 iterations; the CUDA graph the timed call
+        # replays is captured and instantiated here too (setup, not a step)
         eng.iterate(args.warmup, -1.0, "fp32", "sweep")
+        eng.prepare("fp32", "sweep")
         torch.cuda.synchronize()
 
         props = torch.cuda.get_device_properties(dev)
@@ -448,12 +450,15 @@ def run_config(args):
                 fd = (eng.dual_bound(0, tp, tau, "fp64", grad=False)[0] -
                       eng.dual_bound(0, tm, tau, "fp64", grad=False)[0]) / (2 * h)
                 aerrs.append(abs(fd - g[i]))
-                # relative to the coordinate, floored at 1e-6 of the largest component
-                errs.append(abs(fd - g[i]) / max(abs(g[i]), 1e-6 * gscale))
+                # relative error on the coordinates above 1e-3 of the largest: below
+                # that, the central difference's own rounding noise (~eps |F| / h
+                # = 1e-9) dominates; the absolute error covers every coordinate
+                if abs(g[i]) >= 1e-3 * gscale:
+                    errs.append(abs(fd - g[i]) / abs(g[i]))
             out, t = _sync_time(lambda: dual.optimize_dual(eng, 0, tau=tau, steps=200, lr=1e-2, ba_iters=0,
                                                            precision="fp32", theta0=theta0), stream)
             res.update({"n": n, "d": d, "tau": tau, "F": F, "max_D": mD, "dF_dd": gd,
-                        "value_and_grad_ms_fp64": 1000 * tg, "fd_coords": len(errs),
+                        "value_and_grad_ms_fp64": 1000 * tg, "fd_coords": len(aerrs), "fd_rel_coords": len(errs),
                         "fd_max_rel_err": float(np.max(errs)), "fd_median_rel_err": float(np.median(errs)),
                         "fd_max_abs_err": float(np.max(aerrs)), "grad_max_abs": gscale,
                         "ba_lower_after_50": float(eng.history(0)[0][-1]),

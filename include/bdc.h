@@ -124,6 +124,14 @@ void bdc_destroy(bdc_engine *eng);
 bdc_status bdc_ba_iterate(bdc_engine *eng, int max_iters, double gap_tol_bits, int precision, int impl,
                           double *lower, double *upper, int *iters_done);
 
+/* Build, without running it, the CUDA graph that bdc_ba_iterate replays for
+ * this precision and algorithm (use_graph = 1 and a non-NULL stream; a no-op
+ * otherwise), so that the graph's capture and instantiation, a host-side cost
+ * of milliseconds, happen before the first timed call.  Converts the state to
+ * that precision like bdc_ba_iterate; advances no iteration.  Errors:
+ * BDC_EINVAL (bad precision/algorithm), BDC_ECUDA (capture failed). */
+bdc_status bdc_prepare(bdc_engine *eng, int precision, int impl);
+
 /* A batch iterates several bound engines (different n, each with its own d
  * values) from one CUDA graph: every engine's iterations are captured on a
  * stream forked from their common stream, so small instances run

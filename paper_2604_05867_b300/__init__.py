@@ -64,6 +64,7 @@ def lib():
             "bdc_bind": (I, [P, P, SZ, P]),
             "bdc_destroy": (None, [P]),
             "bdc_ba_iterate": (I, [P, I, D, I, I, P, P, P]),
+            "bdc_prepare": (I, [P, I, I]),
             "bdc_get_history": (I, [P, I, P, P, I, P]),
             "bdc_divergence": (I, [P, P, I, P]),
             "bdc_certify_upper": (I, [P, P, P, P, P]),
@@ -170,6 +171,10 @@ class Engine:
         _check(lib().bdc_ba_iterate(self._h, int(max_iters), float(tol), _PREC[precision], _IMPL[impl],
                                     _np_ptr(lo), _np_ptr(up), _np_ptr(it)))
         return lo, up, it
+
+    def prepare(self, precision="fp32", impl="sweep"):
+        """Build the CUDA graph `iterate` replays (bdc_prepare), outside any timed region."""
+        _check(lib().bdc_prepare(self._h, _PREC[precision], _IMPL[impl]))
 
     def history(self, inst: int = 0, length: int = 8192):
         lo = np.zeros(length)

@@ -539,6 +539,22 @@ static bdc_status get_graph(bdc_engine *e, int prec, int impl, cudaGraphExec_t *
     return BDC_OK;
 }
 
+extern "C" bdc_status bdc_prepare(bdc_engine *e, int prec, int impl) {
+    if (!e) BDC_FAIL(BDC_EINVAL, "bdc_prepare: engine is NULL");
+    if (!e->bound) BDC_FAIL(BDC_ENOTBOUND, "bdc_prepare: no workspace bound");
+    if ((prec != BDC_FP32 && prec != BDC_FP64) || (impl != BDC_SWEEP && impl != BDC_LITERAL) ||
+        (impl == BDC_LITERAL && prec != BDC_FP64))
+        BDC_FAIL(BDC_EINVAL, "bdc_prepare: bad precision or impl");
+    if (impl == BDC_LITERAL && !e->orbit_ok)
+        BDC_FAIL(BDC_EINVAL, "bdc_prepare: the literal path needs an orbit-invariant p");
+    BDC_TRY(make_current(e, impl == BDC_LITERAL ? 2 : prec));
+    if (e->opt.use_graph && e->stream != nullptr) {
+        cudaGraphExec_t g;
+        BDC_TRY(get_graph(e, prec, impl, &g));
+    }
+    return sync_check(e, "bdc_prepare");
+}
+
 extern "C" bdc_status bdc_ba_iterate(bdc_engine *e, int max_iters, double tol, int prec, int impl, double *lower,
                                      double *upper, int *iters_done) {
     if (!e) BDC_FAIL(BDC_EINVAL, "bdc_ba_iterate: engine is NULL");
@@ -1076,12 +1092,14 @@ static bdc_status time_sweeps(bdc_engine *e, PrecBuf<T> &b, int reps, float *ms)
     BDC_CUDA_TRY(cudaEventCreate(&a));
     BDC_CUDA_TRY(cudaEventCreate(&z));
     bdc_status st = BDC_OK;
-    // one untimed pass (first touch), then `reps` timed forward + adjoint sweeps;
-    // no update is applied, D is overwritten (the caller materialised p first)
+    // one untimed pass (first touch), then `reps` timed forward + adjoint sweeps
+    // as a BA iteration runs them (complement half mode where it applies); no
+    // update is applied, D is overwritten (the caller materialised p first)
+    const bool half = e->opt.use_half && e->half_ok && half_possible(b.s);
     for (int r = 0; r <= reps && st == BDC_OK; r++) {
         if (r == 1) cudaEventRecord(a, e->stream);
-        st = sweep_forward<T>(e, b, b.p, 0, MODE_ITER);
-        if (st == BDC_OK) st = sweep_adjoint<T>(e, b, b.L, b.omega, b.D, MODE_ITER);
+        st = sweep_forward<T>(e, b, b.p, 0, MODE_ITER, half);
+        if (st == BDC_OK) st = sweep_adjoint<T>(e, b, b.L, b.omega, b.D, MODE_ITER, half);
     }
     cudaEventRecord(z, e->stream);
     cudaError_t err = cudaEventSynchronize(z);

@@ -649,6 +649,20 @@ __global__ void __launch_bounds__(SW_THREADS, tile_blocks<T>(2 * R * SW_THREADS 
     }
 }
 
+// forward rows output: codes c2 < 32 of row c1 go to the transposed Ts, the
+// others to Tm row c1 (16-byte stores)
+template <typename T, int NT>
+__device__ __forceinline__ void store_row_T(const T *buf, T *__restrict__ Tmz, T *__restrict__ Tsz, uint32_t c1, int n1,
+                                            int n2) {
+    if (threadIdx.x + 1 < min(32u, 1u << n2)) Tsz[((size_t)(threadIdx.x + 1) << (n1 + 1)) + c1] = buf[threadIdx.x + 1];
+    T *row = Tmz + ((size_t)c1 << n2);
+    for (uint32_t c2 = 32 + 4 * threadIdx.x; c2 < (1u << n2); c2 += 4 * NT) {
+        T t4[4];
+        ld4(buf + c2, t4);
+        st4(row + c2, t4);
+    }
+}
+
 // pass 2 forward (rows): one row c1 per CTA; input row = F1[c1] (c1 < 2^n1)
 // or p[x1 = c1 - 2^n1]; output codes c2 < 32 go to the transposed Ts.
 template <typename T, int R, bool HALF>
@@ -683,10 +697,8 @@ __global__ void __launch_bounds__(SW_THREADS, tile_blocks<T>(2 * R * SW_THREADS 
     lsweep_fwd_any<T, R>(buf, n2, 0);
     T *Tmz = Tm + z * a.strideM;
     T *Tsz = Ts + z * ((size_t)32 << (n1 + 1));
-    for (uint32_t c2 = threadIdx.x + 1; c2 < half; c2 += SW_THREADS) {
-        if (c2 < 32) Tsz[((size_t)c2 << (n1 + 1)) + c1] = buf[c2];
-        else Tmz[((size_t)c1 << n2) + c2] = buf[c2];
-    }
+    store_row_T<T, SW_THREADS>(buf, Tmz, Tsz, c1, n1, n2);
+    (void)half;
 }
 
 // combine: F_n(y) = sum over splits of the two passes' outputs; q_k = F_n / C(n,k)
@@ -1146,10 +1158,7 @@ __global__ void __launch_bounds__(1 << LT) k_rows_fwd_l(SweepArgs a, const T *p,
     lsweep_fwd_any<T, NI, ROW_THREADS>(buf, n2, 0, NL);
     T *Tmz = Tm + z * a.strideM;
     T *Tsz = Ts + z * ((size_t)32 << (n1 + 1));
-    for (uint32_t c2 = threadIdx.x + 1; c2 < half; c2 += ROW_THREADS) {
-        if (c2 < 32) Tsz[((size_t)c2 << (n1 + 1)) + c1] = buf[c2];
-        else Tmz[((size_t)c1 << n2) + c2] = buf[c2];
-    }
+    store_row_T<T, ROW_THREADS>(buf, Tmz, Tsz, c1, n1, n2);
 }
 
 template <typename T, int NL, bool HALF, int LT>

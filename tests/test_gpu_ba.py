@@ -289,3 +289,22 @@ def test_register_steps_match_oracle():
     p = eng.get_p()[0]
     assert np.all(np.abs(p - pr) <= 1e-9 * pr)
     eng.close()
+
+
+def test_prepared_graph_matches_stream_launches():
+    # bdc_prepare builds the replayed graph ahead of time; replaying it gives
+    # the same iterations, bit for bit, as launching every kernel on the stream
+    import paper_2604_05867_b300 as bdc
+    n, d, T = 16, 0.5, 16
+    a = bdc.Engine(n, [d], options=bdc.default_options(chunk=8))
+    b = bdc.Engine(n, [d], options=bdc.default_options(chunk=8, use_graph=0))
+    a.prepare("fp32", "sweep")
+    launches = a.launch_count()
+    a.iterate(T, -1.0, "fp32", "sweep")
+    b.iterate(T, -1.0, "fp32", "sweep")
+    la, ua = a.history(0)
+    lb, ub = b.history(0)
+    assert np.array_equal(la, lb) and np.array_equal(ua, ub)
+    assert np.array_equal(a.get_p(), b.get_p())
+    a.close()
+    b.close()
