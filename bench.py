@@ -61,6 +61,9 @@ def stage_bytes(n: int, n1: int, n2: int, elem: int, half: bool) -> dict:
         "rows_adj": 4 * N * elem,
         # Gb, Hb, p in, D out (single pass: L, Hb, p in, D out)
         "cols_adj": 5 * N * elem,
+        # the iteration boundary in one pass: Gb (every row), Hb, p in; updated p
+        # and the next iteration's F1 out (D is not stored)
+        "cols_step": 6 * N * elem,
         "symmetrize": 2 * N * elem,  # reads and writes the stored half
         "finalize": 0,
     }

@@ -82,6 +82,14 @@ typedef struct {
      * the forward (4) and adjoint (8) columns passes, where the tile shape
      * allows.  Default 15; 0 keeps every step in shared memory. */
     int use_regsteps;
+    /* Where the register-resident column kernels apply (bits 4 and 8 of
+     * use_regsteps), run each BA iteration's boundary in one pass: the adjoint
+     * columns pass of iteration t also applies the update and runs the
+     * forward columns pass of t+1.  The orbit mean of D is then not taken
+     * each iteration (the iterates are plain BA iterates, up to rounding);
+     * the orbit mean of p is taken whenever the state is read, so p read back
+     * is exactly orbit-invariant.  Default 1. */
+    int fuse_update;
 } bdc_options;
 
 /* Fill *opt with the defaults above. */

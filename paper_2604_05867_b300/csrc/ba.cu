@@ -43,16 +43,18 @@ __global__ void k_build_Hb(int n, int nd, const uint32_t *reps, int64_t R, const
     }
 }
 
-// one block per instance; partials reduced in a fixed order (deterministic)
+// one block per instance; partials reduced in a fixed order (deterministic).
+// stepped: the update was applied in the adjoint columns pass (which also
+// summed p into slot 1 [2]), so nothing is left pending
 __global__ void k_finalize_iter(int nd, const double *part, int maxblk, int nblk0, int nblk1, double *inst,
-                                double *hist) {
+                                double *hist, int stepped) {
     __shared__ double red[FIN_THREADS / 32];
     const int z = blockIdx.x;
     double *I = inst + z * INST_STRIDE;
     if (I[I_ACTIVE] == 0.0) return;
     const double *p0 = part + ((size_t)z * 2 + 0) * maxblk * 4;
     const double *p1 = part + ((size_t)z * 2 + 1) * maxblk * 4;
-    double Zp = fin_sum(p0, 4, nblk0, red);
+    double Zp = stepped ? fin_sum(p1 + 2, 4, nblk1, red) : fin_sum(p0, 4, nblk0, red);
     double ZD = fin_sum(p1, 4, nblk1, red);
     double mD = fin_max(p1 + 1, 4, nblk1, red);
     if (threadIdx.x != 0) return;
@@ -68,8 +70,8 @@ __global__ void k_finalize_iter(int nd, const double *part, int maxblk, int nblk
     I[I_ZP] = Zp;
     I[I_MAXD] = mD;
     I[I_SHIFT] = log2(ZD);
-    I[I_PENDING] = 1.0;
-    I[I_SYMNEED] = 1.0;
+    I[I_PENDING] = stepped ? 0.0 : 1.0;
+    I[I_SYMNEED] = stepped ? 0.0 : 1.0;
     I[I_ITERS] += 1.0;
     long h = (long)I[I_HISTN];
     hist[((size_t)z * 2 + 0) * BDC_HIST + (h % BDC_HIST)] = lower;
@@ -98,11 +100,11 @@ __global__ void k_finalize_sum(int nd, const double *part, int maxblk, int nblk,
 // n2h > 0: complement half mode, only inputs whose bit (n2h-1) is 0 are
 // stored and written; the others are read as their complements
 template <typename T>
-__global__ void k_symmetrize(int n, T *D, const double *inst, int n2h) {
+__global__ void k_symmetrize(int n, T *D, const double *inst, int n2h, int force) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *tile = reinterpret_cast<T *>(smem_raw);
     const int z = blockIdx.y;
-    if (inst[z * INST_STRIDE + I_SYMNEED] == 0.0) return;
+    if (!force && inst[z * INST_STRIDE + I_SYMNEED] == 0.0) return;
     const int hb = min(5, n / 2), nm = n - 2 * hb;
     const uint32_t H = 1u << hb, TS = H * H;
     const uint32_t mid = blockIdx.x;
@@ -308,11 +310,12 @@ bdc_status launch_build_Hb_w(bdc_engine *e, const double *w, double *out) {
 }
 
 template <typename T>
-bdc_status launch_finalize(bdc_engine *e, PrecBuf<T> &b, int mode, int add_negh, int nblk) {
+bdc_status launch_finalize(bdc_engine *e, PrecBuf<T> &b, int mode, int add_negh, int nblk, int stepped) {
     int maxblk = part_maxblk(e);
     if (nblk <= 0) nblk = b.s.nblk_cols;
     if (mode == MODE_ITER) {
-        k_finalize_iter<<<e->nd, FIN_THREADS, 0, e->stream>>>(e->nd, b.part, maxblk, nblk, nblk, e->inst, e->hist); e->launches++; stage_mark(e, "finalize");
+        k_finalize_iter<<<e->nd, FIN_THREADS, 0, e->stream>>>(e->nd, b.part, maxblk, nblk, nblk, e->inst, e->hist,
+                                                              stepped); e->launches++; stage_mark(e, "finalize");
     } else {
         k_finalize_sum<<<e->nd, FIN_THREADS, 0, e->stream>>>(e->nd, b.part, maxblk, b.s.nblk_cols, e->inst,
                                                              add_negh); e->launches++;
@@ -323,7 +326,7 @@ bdc_status launch_finalize(bdc_engine *e, PrecBuf<T> &b, int mode, int add_negh,
 
 bdc_status launch_finalize_literal(bdc_engine *e, int nblk0, int nblk1) {
     k_finalize_iter<<<e->nd, FIN_THREADS, 0, e->stream>>>(e->nd, e->f64.part, part_maxblk(e), nblk0, nblk1, e->inst,
-                                                          e->hist); e->launches++; stage_mark(e, "finalize");
+                                                          e->hist, 0); e->launches++; stage_mark(e, "finalize");
     BDC_CUDA_TRY(cudaGetLastError());
     return BDC_OK;
 }
@@ -336,13 +339,16 @@ bdc_status launch_mirror_half(bdc_engine *e, T *a, int n2) {
 }
 
 template <typename T>
-bdc_status launch_symmetrize(bdc_engine *e, T *D, int n2h) {
+bdc_status launch_symmetrize(bdc_engine *e, T *D, int n2h, bool force) {
     const int n = e->n;
     const int hb = std::min(5, n / 2), nm = n - 2 * hb;
     size_t smem = (size_t)4 * ((size_t)1 << hb) * (((size_t)1 << hb) + 1) * sizeof(T);
     dim3 g(1u << nm, e->nd);
-    k_symmetrize<T><<<g, 256, smem, e->stream>>>(n, D, e->inst, n2h); e->launches++;
-    k_clear_symneed<<<(e->nd + 63) / 64, 64, 0, e->stream>>>(e->nd, e->inst); e->launches++; stage_mark(e, "symmetrize");
+    k_symmetrize<T><<<g, 256, smem, e->stream>>>(n, D, e->inst, n2h, force ? 1 : 0); e->launches++;
+    if (!force) {
+        k_clear_symneed<<<(e->nd + 63) / 64, 64, 0, e->stream>>>(e->nd, e->inst); e->launches++;
+    }
+    stage_mark(e, "symmetrize");
     BDC_CUDA_TRY(cudaGetLastError());
     return BDC_OK;
 }
@@ -351,6 +357,12 @@ template <typename T>
 bdc_status launch_apply_pending(bdc_engine *e, PrecBuf<T> &b) {
     k_apply_pending<T><<<grid_for((size_t)1 << e->n, 256), 256, 0, e->stream>>>(e->n, e->nd, b.p, b.D, e->inst); e->launches++;
     k_clear_pending<<<(e->nd + 63) / 64, 64, 0, e->stream>>>(e->nd, e->inst); e->launches++;
+    BDC_CUDA_TRY(cudaGetLastError());
+    return BDC_OK;
+}
+
+bdc_status launch_clear_symneed(bdc_engine *e) {
+    k_clear_symneed<<<(e->nd + 63) / 64, 64, 0, e->stream>>>(e->nd, e->inst); e->launches++;
     BDC_CUDA_TRY(cudaGetLastError());
     return BDC_OK;
 }
@@ -387,10 +399,10 @@ bdc_status launch_expand_reps(bdc_engine *e, const double *Dr, double *out) {
 
 template bdc_status launch_build_Hb<float>(bdc_engine *, PrecBuf<float> &);
 template bdc_status launch_build_Hb<double>(bdc_engine *, PrecBuf<double> &);
-template bdc_status launch_finalize<float>(bdc_engine *, PrecBuf<float> &, int, int, int);
-template bdc_status launch_finalize<double>(bdc_engine *, PrecBuf<double> &, int, int, int);
-template bdc_status launch_symmetrize<float>(bdc_engine *, float *, int);
-template bdc_status launch_symmetrize<double>(bdc_engine *, double *, int);
+template bdc_status launch_finalize<float>(bdc_engine *, PrecBuf<float> &, int, int, int, int);
+template bdc_status launch_finalize<double>(bdc_engine *, PrecBuf<double> &, int, int, int, int);
+template bdc_status launch_symmetrize<float>(bdc_engine *, float *, int, bool);
+template bdc_status launch_symmetrize<double>(bdc_engine *, double *, int, bool);
 template bdc_status launch_mirror_half<float>(bdc_engine *, float *, int);
 template bdc_status launch_mirror_half<double>(bdc_engine *, double *, int);
 template bdc_status launch_apply_pending<float>(bdc_engine *, PrecBuf<float> &);

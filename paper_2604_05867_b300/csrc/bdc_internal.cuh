@@ -146,6 +146,8 @@ struct bdc_engine {
     bool half_ok = true;        // p is complement-invariant (uniform start, BA iterates)
     bool orbit_ok = true;       // p is invariant under complement and reversal
     bool half_active[2] = {false, false};  // upper half of p/D stale in that precision
+    bool f1_current[2] = {false, false};   // F1 holds the forward columns pass of the current p
+    bool p_unsym[2] = {false, false};      // stepped iterations ran since p was last orbit-averaged
     int half_n2[2] = {0, 0};    // n2 of the schedule the half mode ran with
     int64_t iters_total = 0;
     int64_t launches = 0;       // kernels launched so far (graph replays included)
@@ -176,20 +178,24 @@ template <typename T>
 bdc_status sweep_prepare(bdc_engine *e, PrecBuf<T> &b);
 template <typename T>
 bdc_status sweep_forward(bdc_engine *e, PrecBuf<T> &b, const T *p_src, int apply_update, int mode, bool half = false,
-                         bool sym_rev = false);
+                         bool sym_rev = false, bool cols = true, bool rest = true);
 template <typename T>
 bdc_status sweep_adjoint(bdc_engine *e, PrecBuf<T> &b, const T *Lsrc, const T *omega, T *Dout, int mode,
-                         bool half = false);
+                         bool half = false, bool step = false);
 bool half_possible(const Sched &s);
+// the adjoint columns pass can carry the BA update and the next forward
+// columns pass (register-resident column kernels apply)
+template <typename T>
+bool step_possible(const bdc_engine *e, const Sched &s);
 
 // BA glue (ba.cu)
 template <typename T>
 bdc_status launch_build_Hb(bdc_engine *e, PrecBuf<T> &b);
 bdc_status launch_build_Hb_w(bdc_engine *e, const double *w, double *out);
 template <typename T>
-bdc_status launch_finalize(bdc_engine *e, PrecBuf<T> &b, int mode, int add_negh = 0, int nblk = 0);
+bdc_status launch_finalize(bdc_engine *e, PrecBuf<T> &b, int mode, int add_negh = 0, int nblk = 0, int stepped = 0);
 template <typename T>
-bdc_status launch_symmetrize(bdc_engine *e, T *D, int n2h = 0);
+bdc_status launch_symmetrize(bdc_engine *e, T *D, int n2h = 0, bool force = false);
 template <typename T>
 bdc_status launch_mirror_half(bdc_engine *e, T *a, int n2);
 template <typename T>
@@ -197,6 +203,7 @@ bdc_status launch_apply_pending(bdc_engine *e, PrecBuf<T> &b);
 bdc_status launch_literal_update(bdc_engine *e);
 bdc_status launch_literal_reduce(bdc_engine *e);
 bdc_status launch_clear_pending(bdc_engine *e);
+bdc_status launch_clear_symneed(bdc_engine *e);
 bdc_status launch_finalize_literal(bdc_engine *e, int nblk0, int nblk1);
 bdc_status launch_expand_reps(bdc_engine *e, const double *Dr, double *out);
 int literal_grid(const bdc_engine *e);

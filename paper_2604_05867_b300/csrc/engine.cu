@@ -239,6 +239,7 @@ extern "C" void bdc_default_options(bdc_options *o) {
     o->enable_literal = 1;
     o->use_half = 1;
     o->use_regsteps = 15;
+    o->fuse_update = 1;
 }
 
 extern "C" bdc_status bdc_create(int n, const double *d, int nd, const bdc_options *opt, bdc_engine **out) {
@@ -425,6 +426,7 @@ static bdc_status unhalf(bdc_engine *e) {
     const bool sym = e->opt.symmetrize && e->orbit_ok;
     if (sym && e->cur == 0 && e->half_active[0]) BDC_TRY(launch_symmetrize<float>(e, e->f32.D, e->half_n2[0]));
     if (sym && e->cur == 1 && e->half_active[1]) BDC_TRY(launch_symmetrize<double>(e, e->f64.D, e->half_n2[1]));
+    if (e->half_active[0] || e->half_active[1]) e->f1_current[0] = e->f1_current[1] = false;
     if (e->half_active[0]) {
         BDC_TRY(launch_mirror_half<float>(e, e->f32.p, e->half_n2[0]));
         BDC_TRY(launch_mirror_half<float>(e, e->f32.D, e->half_n2[0]));
@@ -448,6 +450,17 @@ static void drop_graphs(bdc_engine *e) {
 }
 
 static bdc_status materialize(bdc_engine *e) {
+    // stepped iterations owe the orbit mean of p (they apply the update without
+    // averaging D over orbits): take it now, bit-identical over every orbit
+    if (e->cur <= 1 && e->p_unsym[e->cur]) {
+        if (e->opt.symmetrize && e->orbit_ok) {
+            const int n2h = e->half_active[e->cur] ? e->half_n2[e->cur] : 0;
+            if (e->cur == 0) BDC_TRY(launch_symmetrize<float>(e, e->f32.p, n2h, true));
+            else BDC_TRY(launch_symmetrize<double>(e, e->f64.p, n2h, true));
+        }
+        e->p_unsym[e->cur] = false;
+    }
+    e->f1_current[0] = e->f1_current[1] = false;
     BDC_TRY(unhalf(e));
     BDC_TRY(activate(e, -1.0));
     if (e->cur == 0) return launch_apply_pending<float>(e, e->f32);
@@ -475,20 +488,65 @@ static bdc_status make_current(bdc_engine *e, int target) {
     }
     BDC_CUDA_TRY(cudaGetLastError());
     e->cur = target;
+    e->p_unsym[0] = e->p_unsym[1] = false;  // the new copy comes from the averaged p
     return BDC_OK;
 }
 
 // ---------------------------------------------------------------------------
 // iteration
 // ---------------------------------------------------------------------------
+// Stepped iterations (the adjoint columns pass applies the update and runs
+// the next forward columns pass) need F1 to hold the forward columns pass of
+// the current p: run that pass alone.  It applies a pending update (with the
+// orbit mean of D in half mode), after which nothing is pending.
+template <typename T>
+static bdc_status prime_step(bdc_engine *e, PrecBuf<T> &b, int prec, bool half) {
+    const bool sym = e->opt.symmetrize && e->orbit_ok;
+    BDC_TRY(sweep_forward<T>(e, b, b.p, 1, MODE_ITER, half, half && sym, true, false));
+    BDC_TRY(launch_clear_pending(e));
+    BDC_TRY(launch_clear_symneed(e));
+    if (half) {
+        e->half_active[prec] = true;
+        e->half_n2[prec] = b.s.n2;
+    }
+    e->f1_current[prec] = true;
+    return BDC_OK;
+}
+
+static bdc_status ensure_primed(bdc_engine *e, int prec) {
+    if (prec == BDC_FP32) {
+        PrecBuf<float> &b = e->f32;
+        if (step_possible<float>(e, b.s) && !e->f1_current[0])
+            return prime_step<float>(e, b, 0, e->opt.use_half && e->half_ok && half_possible(b.s));
+    } else {
+        PrecBuf<double> &b = e->f64;
+        if (step_possible<double>(e, b.s) && !e->f1_current[1])
+            return prime_step<double>(e, b, 1, e->opt.use_half && e->half_ok && half_possible(b.s));
+    }
+    return BDC_OK;
+}
+
 template <typename T>
 static bdc_status iter_sweep(bdc_engine *e, PrecBuf<T> &b, int prec) {
     // complement half mode while p is complement-invariant
     const bool half = e->opt.use_half && e->half_ok && half_possible(b.s);
     if (!half && e->half_active[prec]) BDC_TRY(unhalf(e));
+    const bool sym = e->opt.symmetrize && e->orbit_ok;
+    if (step_possible<T>(e, b.s)) {
+        if (!e->f1_current[prec]) BDC_TRY(prime_step<T>(e, b, prec, half));
+        BDC_TRY(sweep_forward<T>(e, b, b.p, 1, MODE_ITER, half, false, false));
+        BDC_TRY(sweep_adjoint<T>(e, b, b.L, b.omega, b.D, MODE_ITER, half, true));
+        BDC_TRY(launch_finalize<T>(e, b, MODE_ITER, 0, half ? b.s.nblk_cols / 2 : b.s.nblk_cols, 1));
+        e->f1_current[prec] = true;
+        e->p_unsym[prec] = true;
+        if (half) {
+            e->half_active[prec] = true;
+            e->half_n2[prec] = b.s.n2;
+        }
+        return BDC_OK;
+    }
     // orbit mean of D: in half mode fused into the next forward pass (and into
     // unhalf), otherwise a pass of its own
-    const bool sym = e->opt.symmetrize && e->orbit_ok;
     BDC_TRY(sweep_forward<T>(e, b, b.p, 1, MODE_ITER, half, half && sym));
     BDC_TRY(sweep_adjoint<T>(e, b, b.L, b.omega, b.D, MODE_ITER, half));
     BDC_TRY(launch_finalize<T>(e, b, MODE_ITER, 0, half ? b.s.nblk_cols / 2 : b.s.nblk_cols));
@@ -517,6 +575,8 @@ static bdc_status iter_once(bdc_engine *e, int prec, int impl) {
 
 static bdc_status get_graph(bdc_engine *e, int prec, int impl, cudaGraphExec_t *out) {
     cudaGraphExec_t &g = e->graph[prec][impl];
+    // a graph of stepped iterations starts from a current F1 (eager, not captured)
+    if (impl == BDC_SWEEP) BDC_TRY(ensure_primed(e, prec));
     if (!g) {
         cudaGraph_t graph;
         const int64_t before = e->launches;
@@ -672,6 +732,7 @@ static bdc_status batch_graph(bdc_batch *b, int prec, cudaGraphExec_t *out) {
     if (!b->graph[prec]) {
         cudaGraph_t graph;
         std::vector<int64_t> before(b->engs.size());
+        for (bdc_engine *e : b->engs) BDC_TRY(ensure_primed(e, prec));
         BDC_CUDA_TRY(cudaStreamBeginCapture(b->main, cudaStreamCaptureModeThreadLocal));
         bdc_status st = BDC_OK;
         cudaError_t ce = cudaEventRecord(b->fork, b->main);
@@ -718,6 +779,7 @@ extern "C" bdc_status bdc_batch_iterate(bdc_batch *b, int max_iters, double tol,
     int done = 0;
     std::vector<double> h;
     while (done < max_iters) {
+        for (bdc_engine *e : b->engs) BDC_TRY(ensure_primed(e, prec));
         BDC_CUDA_TRY(cudaGraphLaunch(g, b->main));
         b->engs[0]->launches += b->graph_kernels[prec];
         done += b->chunk;
@@ -919,6 +981,8 @@ static bdc_status upload_p(bdc_engine *e, const double *p_host, bool normalize) 
     e->half_ok = sym;
     e->orbit_ok = orb;
     e->half_active[0] = e->half_active[1] = false;
+    e->f1_current[0] = e->f1_current[1] = false;
+    e->p_unsym[0] = e->p_unsym[1] = false;
     BDC_CUDA_TRY(cudaMemcpyAsync(e->f64.p, p.data(), cnt * sizeof(double), cudaMemcpyHostToDevice, e->stream));
     BDC_TRY(sync_check(e, "bdc_set_p upload"));
     const int g = grid_for(cnt, 256);

@@ -1043,12 +1043,19 @@ k_cols_fwd_l(SweepArgs a, T *__restrict__ p, const T *__restrict__ D, T *__restr
     }
 }
 
-template <typename T, int NL, bool HALF>
+// STEP: the iteration boundary in one pass over the tile.  After D and the
+// bounds' partial sums of iteration t, the BA update p <- p 2^(D - s) is
+// applied in registers (s: the previous iteration's log2 normaliser; p is kept
+// unnormalised and its sum is tracked, so any s is exact) and the forward
+// columns pass of iteration t+1 runs on the updated inputs, writing F1.  D is
+// not stored.
+template <typename T, int NL, bool HALF, bool STEP>
 __global__ void __launch_bounds__(SW_THREADS, tile_blocks<T>((size_t)SW_THREADS * (2 << NL) * sizeof(T), 2))
-k_cols_adj_l(SweepArgs a, EpiArgs ep, const T *__restrict__ Gb) {
+k_cols_adj_l(SweepArgs a, EpiArgs ep, const T *__restrict__ Gb, T *__restrict__ pw, T *__restrict__ F1) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *buf = reinterpret_cast<T *>(smem_raw);
     __shared__ T red[2 * SW_THREADS / 32];
+    __shared__ T red2[2 * SW_THREADS / 32];
     constexpr int NI = 1 << NL;
     const int z = blockIdx.y;
     if (!flag_set(a.inst + z * INST_STRIDE, I_ACTIVE)) return;
@@ -1092,8 +1099,9 @@ k_cols_adj_l(SweepArgs a, EpiArgs ep, const T *__restrict__ Gb) {
     for (int r = 1; r < 2 * NI; r++) v[r] = buf[((((uint32_t)r << L) | sigma) << lw) | c];
     local_adj<T, NL>(v);
     const T *__restrict__ Hbz = reinterpret_cast<const T *>(ep.Hb) + z * a.strideN;
-    const T *__restrict__ pz = reinterpret_cast<const T *>(ep.p) + z * a.strideN;
-    T *__restrict__ Dz = reinterpret_cast<T *>(ep.Dout) + z * a.strideN;
+    // (STEP reads and rewrites p through this one pointer)
+    T *__restrict__ pz = (STEP ? pw : const_cast<T *>(reinterpret_cast<const T *>(ep.p))) + z * a.strideN;
+    T *__restrict__ Dz = STEP ? nullptr : reinterpret_cast<T *>(ep.Dout) + z * a.strideN;
     // all of a thread's global loads are issued before its first store, in two
     // rounds that fit the registers: Hb into the rows below 2^NL of v (dead
     // after the local steps), D = -Hb - G there, then p over the G rows
@@ -1111,15 +1119,61 @@ k_cols_adj_l(SweepArgs a, EpiArgs ep, const T *__restrict__ Gb) {
         tZ += v[NI + r] * exp2_t<T>(Dv);
         tM = Dv > tM ? Dv : tM;
     }
+    if constexpr (!STEP) {
 #pragma unroll
-    for (int r = 0; r < NI; r++) Dz[x0 + r * xs] = v[r];
-    block_sum_max_t<T>(tZ, tM, red);
-    if (threadIdx.x == 0) {
-        double *pp = a.part + ((size_t)z * 2 + 1) * a.maxblk * 4 + blockIdx.x * 4;
-        pp[0] = (double)tZ * (HALF ? 2.0 : 1.0);  // each column also stands for its complement
-        pp[1] = (double)tM;
-        pp[2] = 0.0;
-        pp[3] = -INFINITY;
+        for (int r = 0; r < NI; r++) Dz[x0 + r * xs] = v[r];
+        block_sum_max_t<T>(tZ, tM, red);
+        if (threadIdx.x == 0) {
+            double *pp = a.part + ((size_t)z * 2 + 1) * a.maxblk * 4 + blockIdx.x * 4;
+            pp[0] = (double)tZ * (HALF ? 2.0 : 1.0);  // each column also stands for its complement
+            pp[1] = (double)tM;
+            pp[2] = 0.0;
+            pp[3] = -INFINITY;
+        }
+    } else {
+        (void)Dz;
+        T tP = (T)0;
+#pragma unroll
+        for (int r = 0; r < NI; r++) tP += v[NI + r];
+        const T shift = (T)a.inst[z * INST_STRIDE + I_SHIFT];
+#pragma unroll
+        for (int r = 0; r < NI; r++) v[NI + r] = v[NI + r] * exp2_t<T>(v[r] - shift);
+#pragma unroll
+        for (int r = 0; r < NI; r++) pz[x0 + r * xs] = v[NI + r];
+        block_sum_max_t<T>(tZ, tM, red);
+        T unused = (T)0;
+        block_sum_max_t<T>(tP, unused, red2);
+        if (threadIdx.x == 0) {
+            double *pp = a.part + ((size_t)z * 2 + 1) * a.maxblk * 4 + blockIdx.x * 4;
+            pp[0] = (double)tZ * (HALF ? 2.0 : 1.0);  // each column also stands for its complement
+            pp[1] = (double)tM;
+            pp[2] = (double)tP * (HALF ? 2.0 : 1.0);
+            pp[3] = -INFINITY;
+        }
+        // forward columns pass of the next iteration on the updated inputs
+        local_fwd<T, NL>(v);
+        __syncthreads();  // every thread has read its adjoint rows from buf
+#pragma unroll
+        for (int r = 1; r < 2 * NI; r++) buf[((((uint32_t)r << L) | sigma) << lw) | c] = v[r];
+        buf[(sigma << lw) | c] = (T)0;  // rows [0, 2^L) start the shared-memory steps at 0
+        __syncthreads();
+        lsweep_fwd_any<T, NI>(buf, n1, lw, NL);
+        T *Fz = F1 + z * a.strideN;
+        const uint32_t ntop = (1u << n1) << lw;
+        if (lw >= 2) {
+#pragma unroll 4
+            for (uint32_t e = w + 4 * threadIdx.x; e < ntop; e += 4 * SW_THREADS) {
+                uint32_t row = e >> lw, cc = e & (w - 1u);
+                T t4[4];
+                ld4(buf + e, t4);
+                st4(Fz + (((size_t)row << n2) | (col0 + cc)), t4);
+            }
+        } else {
+            for (uint32_t e = threadIdx.x + w; e < ntop; e += SW_THREADS) {
+                uint32_t row = e >> lw, cc = e & (w - 1u);
+                Fz[((size_t)row << n2) | (col0 + cc)] = buf[e];
+            }
+        }
     }
 }
 
@@ -1319,7 +1373,8 @@ cudaError_t prepare_all(size_t cols_bytes, size_t rows_bytes) {
     PREP_ONE(1) PREP_ONE(2) PREP_ONE(4) PREP_ONE(8) PREP_ONE(16) PREP_ONE(32) PREP_ONE(64)
 #define PREP_L(NL, H)                                                                        \
     if (err == cudaSuccess) err = allow_smem(k_cols_fwd_l<T, NL, H>, cols_bytes);            \
-    if (err == cudaSuccess) err = allow_smem(k_cols_adj_l<T, NL, H>, cols_bytes);            \
+    if (err == cudaSuccess) err = allow_smem(k_cols_adj_l<T, NL, H, false>, cols_bytes);     \
+    if (err == cudaSuccess) err = allow_smem(k_cols_adj_l<T, NL, H, true>, cols_bytes);      \
     if (err == cudaSuccess) err = allow_smem(k_rows_adj_l<T, NL, H, 9>, rows_bytes);
     PREP_L(3, false) PREP_L(3, true) PREP_L(4, false) PREP_L(4, true)
     if constexpr (sizeof(T) == 4) { PREP_L(5, false) PREP_L(5, true) }
@@ -1367,8 +1422,13 @@ static int nl_rows_adj(const bdc_engine *e, const Sched &s) {
 }
 
 template <typename T>
+bool step_possible(const bdc_engine *e, const Sched &s) {
+    return e->opt.fuse_update && nl_cols<T>(e, s, 4) && nl_cols<T>(e, s, 8);
+}
+
+template <typename T>
 bdc_status sweep_forward(bdc_engine *e, PrecBuf<T> &b, const T *p_src, int apply_update, int mode, bool half,
-                         bool sym_rev) {
+                         bool sym_rev, bool cols, bool rest) {
     SweepArgs a = make_args(e, b);
     const Sched &s = b.s;
     half = half && half_possible(s);
@@ -1377,7 +1437,9 @@ bdc_status sweep_forward(bdc_engine *e, PrecBuf<T> &b, const T *p_src, int apply
     dim3 g1(half ? s.nblk_cols / 2 : s.nblk_cols, e->nd);
     const int rc = r_of(((size_t)1 << s.n1) << s.lw);
     const int nlc = (mode == MODE_ITER) ? nl_cols<T>(e, s, 4) : 0;
-    if (nlc && half)
+    if (!cols && s.n2 > 0) {
+        // F1 is current (written by the previous stepped adjoint pass)
+    } else if (nlc && half)
         SW_WITH_NL(T, nlc, (k_cols_fwd_l<T, NL, true><<<g1, SW_THREADS, sm1, e->stream>>>(
                                a, p, b.D, b.F1, apply_update, sym_rev ? 1 : 0)));
     else if (nlc)
@@ -1389,8 +1451,12 @@ bdc_status sweep_forward(bdc_engine *e, PrecBuf<T> &b, const T *p_src, int apply
     else
         SW_WITH_R(rmax_fwd<T>(), rc, (k_cols_fwd<T, R, false><<<g1, SW_THREADS, sm1, e->stream>>>(
                                          a, p, b.D, b.F1, b.q, b.L, apply_update, mode, 0)));
-    e->launches++; stage_mark(e, "cols_fwd");
-    BDC_CUDA_TRY(cudaGetLastError());
+    if (cols || s.n2 == 0) {
+        e->launches++; stage_mark(e, "cols_fwd");
+        BDC_CUDA_TRY(cudaGetLastError());
+        e->f1_current[sizeof(T) == 4 ? 0 : 1] = false;  // F1 now holds this pass's p_src / mode
+    }
+    if (!rest) return BDC_OK;
     if (s.n2 > 0) {
         size_t sm2 = tile_bytes_rows<T>(s);
         dim3 g2(half ? (1u << s.n1) : (2u << s.n1) - 1u, e->nd);
@@ -1421,7 +1487,8 @@ bdc_status sweep_forward(bdc_engine *e, PrecBuf<T> &b, const T *p_src, int apply
 }
 
 template <typename T>
-bdc_status sweep_adjoint(bdc_engine *e, PrecBuf<T> &b, const T *Lsrc, const T *omega, T *Dout, int mode, bool half) {
+bdc_status sweep_adjoint(bdc_engine *e, PrecBuf<T> &b, const T *Lsrc, const T *omega, T *Dout, int mode, bool half,
+                         bool step) {
     SweepArgs a = make_args(e, b);
     const Sched &s = b.s;
     half = half && half_possible(s);
@@ -1458,28 +1525,41 @@ bdc_status sweep_adjoint(bdc_engine *e, PrecBuf<T> &b, const T *Lsrc, const T *o
     dim3 g1(half ? s.nblk_cols / 2 : s.nblk_cols, e->nd);
     const int rc = r_of(((size_t)2 << s.n1) << s.lw);
     const int nlc = (mode == MODE_ITER) ? nl_cols<T>(e, s, 8) : 0;
-    if (nlc && half)
-        SW_WITH_NL(T, nlc, (k_cols_adj_l<T, NL, true><<<g1, SW_THREADS, sm1, e->stream>>>(a, ep, b.Gb)));
+    if (step && nlc && half)
+        SW_WITH_NL(T, nlc, (k_cols_adj_l<T, NL, true, true><<<g1, SW_THREADS, sm1, e->stream>>>(a, ep, b.Gb, b.p,
+                                                                                                 b.F1)));
+    else if (step && nlc)
+        SW_WITH_NL(T, nlc, (k_cols_adj_l<T, NL, false, true><<<g1, SW_THREADS, sm1, e->stream>>>(a, ep, b.Gb, b.p,
+                                                                                                  b.F1)));
+    else if (nlc && half)
+        SW_WITH_NL(T, nlc, (k_cols_adj_l<T, NL, true, false><<<g1, SW_THREADS, sm1, e->stream>>>(a, ep, b.Gb,
+                                                                                                  nullptr, nullptr)));
     else if (nlc)
-        SW_WITH_NL(T, nlc, (k_cols_adj_l<T, NL, false><<<g1, SW_THREADS, sm1, e->stream>>>(a, ep, b.Gb)));
+        SW_WITH_NL(T, nlc, (k_cols_adj_l<T, NL, false, false><<<g1, SW_THREADS, sm1, e->stream>>>(a, ep, b.Gb,
+                                                                                                   nullptr, nullptr)));
     else if (half)
         SW_WITH_R(rmax_adj<T>(), rc,
                   (k_cols_adj<T, R, true><<<g1, SW_THREADS, sm1, e->stream>>>(a, ep, b.Gb, Lsrc, omega, mode)));
     else
         SW_WITH_R(rmax_adj<T>(), rc,
                   (k_cols_adj<T, R, false><<<g1, SW_THREADS, sm1, e->stream>>>(a, ep, b.Gb, Lsrc, omega, mode)));
-    e->launches++; stage_mark(e, "cols_adj");
+    e->launches++; stage_mark(e, (step && nlc) ? "cols_step" : "cols_adj");
     BDC_CUDA_TRY(cudaGetLastError());
     return BDC_OK;
 }
 
 template bdc_status sweep_prepare<float>(bdc_engine *, PrecBuf<float> &);
 template bdc_status sweep_prepare<double>(bdc_engine *, PrecBuf<double> &);
-template bdc_status sweep_forward<float>(bdc_engine *, PrecBuf<float> &, const float *, int, int, bool, bool);
-template bdc_status sweep_forward<double>(bdc_engine *, PrecBuf<double> &, const double *, int, int, bool, bool);
-template bdc_status sweep_adjoint<float>(bdc_engine *, PrecBuf<float> &, const float *, const float *, float *, int, bool);
-template bdc_status sweep_adjoint<double>(bdc_engine *, PrecBuf<double> &, const double *, const double *, double *, int,
+template bdc_status sweep_forward<float>(bdc_engine *, PrecBuf<float> &, const float *, int, int, bool, bool, bool,
+                                         bool);
+template bdc_status sweep_forward<double>(bdc_engine *, PrecBuf<double> &, const double *, int, int, bool, bool, bool,
                                           bool);
+template bdc_status sweep_adjoint<float>(bdc_engine *, PrecBuf<float> &, const float *, const float *, float *, int, bool,
+                                         bool);
+template bdc_status sweep_adjoint<double>(bdc_engine *, PrecBuf<double> &, const double *, const double *, double *, int,
+                                          bool, bool);
+template bool step_possible<float>(const bdc_engine *, const Sched &);
+template bool step_possible<double>(const bdc_engine *, const Sched &);
 
 // ---------------------------------------------------------------------------
 // Output marginal without any device allocation.
