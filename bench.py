@@ -69,6 +69,18 @@ def stage_bytes(n: int, n1: int, n2: int, elem: int, half: bool) -> dict:
     }
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of each
+# FP32 iteration kernel, from one ncu capture of this bench's own workload
+# (profiles/<kernel>_n24.md), keyed by stage, n and the (n1, n2, width)
+# schedule.  A kernel changed since its capture must be removed from here.
+MEASURED_TRAFFIC = {
+    ("cols_step", 24, 11, 13, 4): 135.1296e6 + 44.865024e6,
+    ("rows_adj", 24, 11, 13, 4): 74.597888e6 + 34.273536e6,
+    ("combine", 24, 11, 13, 4): 134.209024e6 + 36.688384e6,
+    ("rows_fwd", 24, 11, 13, 4): 67.143936e6 + 20.312576e6,
+}
+
+
 # ----------------------------------------------------------------------------
 # clocks
 # ----------------------------------------------------------------------------
@@ -262,8 +274,9 @@ def run_ours(args, rank: int, world: int):
             peaks = measured_peaks()
             top = max((k for k in stages if k in sb and sb[k] > 0), key=lambda k: stages[k])
             achieved = sb[top] / (stages[top] / 1000.0) / 1e9
+            traffic = MEASURED_TRAFFIC.get((top, n, sched32["n1"], sched32["n2"], sched32["width"]))
             roof = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                    "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                     "peak_source": peaks["source"], "algorithmic_bytes": sb[top],
                     "note": "complement half mode: %s" % half}
             stage_total = sum(stages.values())
