@@ -55,8 +55,9 @@ def stage_bytes(n: int, n1: int, n2: int, elem: int, half: bool) -> dict:
         "cols_fwd": (4 if split else 3) * N * elem + (0 if split else 4 * N * elem),
         # every row (F1 or p) in, bottom half of every row out
         "rows_fwd": 4 * N * elem,
-        # every (u1, u2) pair in once, q and log2 q out
-        "combine": 8 * N * elem,
+        # every (u1, u2) pair in once, the F1/p terms, log2 q of the H1 codes out
+        # (an iteration does not store q)
+        "combine": 5 * N * elem,
         # log2 q in (its re-reads are L2 hits), Gb out
         "rows_adj": 4 * N * elem,
         # Gb, Hb, p in, D out (single pass: L, Hb, p in, D out)
