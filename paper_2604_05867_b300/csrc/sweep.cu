@@ -751,6 +751,70 @@ __global__ void k_combine(SweepArgs a, const T *__restrict__ p, const T *__restr
     }
 }
 
+// The same combine with the codes laid out by length: every CTA holds
+// CMB_CODES consecutive codes of one length k (block 0 all lengths below KB),
+// so the split range, the source array of each split and every shift are
+// uniform across the CTA, and a term costs a few integer operations and one
+// load; each thread takes CMB_CODES / 256 codes, 256 apart.  Codes of length
+// k: 2^(k-1) in half mode (those starting with 0), 2^k otherwise; blocks
+// [2^(k-KB), 2^(k-KB+1)) cover length k.
+constexpr int CMB_LOG = 11, CMB_CODES = 1 << CMB_LOG;
+template <typename T, bool HALF>
+__global__ void __launch_bounds__(256) k_combine_k(SweepArgs a, const T *__restrict__ p, const T *__restrict__ F1,
+                                                   const T *__restrict__ Tm, const T *__restrict__ Ts,
+                                                   T *__restrict__ q, T *__restrict__ L, int mode) {
+    constexpr int KB = CMB_LOG + (HALF ? 1 : 0);
+    const int z = blockIdx.y;
+    if (!flag_set(a.inst + z * INST_STRIDE, I_ACTIVE)) return;
+    const int n1 = a.n1, n2 = a.n2, n = a.n;
+    const T *pz = p + z * a.strideN, *Fz = F1 + z * a.strideN, *Tmz = Tm + z * a.strideM;
+    const T *Tsz = Ts + z * ((size_t)32 << (n1 + 1));
+    T *qz = q + z * a.strideM, *Lz = L + z * a.strideM;
+    const uint32_t hh = 1u << (n2 - 1), full2 = (1u << n2) - 1u;
+    const bool keep_q = mode != MODE_ITER;
+    int kfirst = 0, klast = min(KB - 1, n);
+    if (blockIdx.x > 0) kfirst = klast = KB - 1 + bitlen32(blockIdx.x);
+    for (int k = kfirst; k <= klast; k++) {
+        const uint32_t cnt = (k == 0) ? 1u : (HALF ? 1u << (k - 1) : 1u << k);
+        const uint32_t y0 = (blockIdx.x == 0) ? 0u : (blockIdx.x - (1u << (k - KB))) << CMB_LOG;
+        const int jlo = max(0, k - n2), jhi = min(k, n1);
+#pragma unroll 4
+        for (int r = 0; r < CMB_CODES / 256; r++) {
+            const uint32_t y = y0 + r * 256 + threadIdx.x;
+            if (y >= cnt) break;
+            T acc = (T)0;
+            for (int j = jlo; j <= jhi; j++) {
+                const int l = k - j;
+                uint32_t c1 = (1u << j) | (y >> l);
+                uint32_t u2 = y & ((1u << l) - 1u);
+                T v;
+                if (l == n2) {
+                    if (HALF && u2 >= hh) {  // complement column of the complement row
+                        c1 = c1 ^ ((1u << j) - 1u);
+                        u2 = full2 - u2;
+                    }
+                    v = (j == n1) ? pz[((size_t)(c1 ^ (1u << n1)) << n2) | u2] : Fz[((size_t)c1 << n2) | u2];
+                } else if (l < 5) {
+                    v = Tsz[((size_t)((1u << l) | u2) << (n1 + 1)) + c1];
+                } else {
+                    v = Tmz[((size_t)c1 << n2) + ((1u << l) | u2)];
+                }
+                acc += v;
+            }
+            const uint32_t c = (1u << k) | y;
+            T qv = acc * inv_binom_t<T>(a, k);
+            T lv = log2_t<T>(mode == MODE_CERT ? fmin(qv, (T)1) : fmax(qv, q_floor_t<T>(a)));
+            if (keep_q) qz[c] = qv;
+            Lz[c] = lv;
+            if (HALF && k > 0 && (keep_q || k <= n2)) {
+                const uint32_t cm = c ^ ((1u << k) - 1u);
+                if (keep_q) qz[cm] = qv;
+                Lz[cm] = lv;
+            }
+        }
+    }
+}
+
 // adjoint rows input: buf[c2] = omega_{j+l} L(c1 . u2) for c2 = 2^l + u2
 // (l = |u2|, j = |c1|), buf[0] = 0.  For each length l the codes
 // (c1 << l) + u2 are 2^l contiguous values: 16-byte loads and stores from l = 2.
@@ -1475,11 +1539,11 @@ bdc_status sweep_forward(bdc_engine *e, PrecBuf<T> &b, const T *p_src, int apply
                       (k_rows_fwd<T, R, false><<<g2, SW_THREADS, sm2, e->stream>>>(a, p, b.F1, b.Tm, b.Ts)));
         e->launches++; stage_mark(e, "rows_fwd");
         BDC_CUDA_TRY(cudaGetLastError());
-        size_t outs = half ? ((size_t)1 << e->n) : ((size_t)2 << e->n);
-        int nb = (int)std::min<size_t>(outs / 256 + 1, 148 * 16);
-        dim3 g3(nb, e->nd);
-        if (half) k_combine<T, true><<<g3, 256, 0, e->stream>>>(a, p, b.F1, b.Tm, b.Ts, b.q, b.L, mode);
-        else k_combine<T, false><<<g3, 256, 0, e->stream>>>(a, p, b.F1, b.Tm, b.Ts, b.q, b.L, mode);
+        // blocks of CMB_CODES codes of one length (k_combine_k)
+        const int kb = CMB_LOG + (half ? 1 : 0);
+        dim3 g3(e->n >= kb ? (1u << (e->n - kb + 1)) : 1u, e->nd);
+        if (half) k_combine_k<T, true><<<g3, 256, 0, e->stream>>>(a, p, b.F1, b.Tm, b.Ts, b.q, b.L, mode);
+        else k_combine_k<T, false><<<g3, 256, 0, e->stream>>>(a, p, b.F1, b.Tm, b.Ts, b.q, b.L, mode);
         e->launches++; stage_mark(e, "combine");
         BDC_CUDA_TRY(cudaGetLastError());
     }
