@@ -75,9 +75,7 @@ def stage_bytes(n: int, n1: int, n2: int, elem: int, half: bool) -> dict:
 # (profiles/<kernel>_n24.md), keyed by stage, n and the (n1, n2, width)
 # schedule.  A kernel changed since its capture must be removed from here.
 MEASURED_TRAFFIC = {
-    ("cols_step", 24, 11, 13, 4): 135.1296e6 + 44.865024e6,
     ("rows_adj", 24, 11, 13, 4): 74.597888e6 + 34.273536e6,
-    ("rows_fwd", 24, 11, 13, 4): 67.143936e6 + 20.312576e6,
 }
 
 

@@ -158,6 +158,11 @@ __device__ void lsweep_fwd_cols4(T *buf, int nn, int lw, int ib = 0) {
     for (int i = ib; i < nn; i++) {
         const int m = nn - i - 1;
         const uint32_t row_lo = 1u << m;
+        // the 8 lanes of one 16-byte shared-memory phase hold 32/w consecutive
+        // rows; when the inserted bit lies inside that span, their i0 rows fall
+        // in 4 bank groups twice over.  Lanes 4-7 of each phase then load the
+        // i1 row first, which spreads both loads over all 8 bank groups.
+        const bool spread = (32u >> lw) > row_lo;
 #pragma unroll
         for (int j = 0; j < G; j++) {
             uint32_t g = tid + j * NT;
@@ -165,11 +170,15 @@ __device__ void lsweep_fwd_cols4(T *buf, int nn, int lw, int ib = 0) {
             if (g < ng && P >= row_lo) {
                 uint32_t c = e & cmask;
                 uint32_t i0 = ((P >> m) << (m + 1)) | (P & (row_lo - 1u));
+                const bool swp = spread && ((g >> 2) & 1u);
                 T a[4], b[4];
-                ld4(buf + ((i0 << lw) | c), a);
-                ld4(buf + (((i0 | row_lo) << lw) | c), b);
+                ld4(buf + (((swp ? (i0 | row_lo) : i0) << lw) | c), a);
+                ld4(buf + (((swp ? i0 : (i0 | row_lo)) << lw) | c), b);
 #pragma unroll
-                for (int k = 0; k < 4; k++) own[j][k] = own[j][k] + a[k] + b[k];
+                for (int k = 0; k < 4; k++) {
+                    const T r0 = swp ? b[k] : a[k], r1 = swp ? a[k] : b[k];
+                    own[j][k] = own[j][k] + r0 + r1;
+                }
             }
         }
         __syncthreads();
@@ -202,16 +211,30 @@ __device__ void lsweep_fwd_rows4(T *buf, int nn, int ib = 0) {
             uint32_t P0 = 4 * g;
             if (g < ng && P0 + 3 >= row_lo) {
                 T v[8];
+                // lanes 4-7 of each 16-byte phase load their second chunk first
+                // where the two loads would otherwise meet 4 bank groups twice
+                // (inserted bit below position 5); see lsweep_fwd_cols4
+                const bool swp = ((g >> 2) & 1u) && row_lo < 32u;
                 if (m >= 2) {
                     uint32_t i0 = ((P0 >> m) << (m + 1)) | (P0 & (row_lo - 1u));
-                    ld4(buf + i0, v);
-                    ld4(buf + (i0 | row_lo), v + 4);
+                    T a[4], b[4];
+                    ld4(buf + (swp ? (i0 | row_lo) : i0), a);
+                    ld4(buf + (swp ? i0 : (i0 | row_lo)), b);
 #pragma unroll
-                    for (int k = 0; k < 4; k++) own[j][k] = own[j][k] + v[k] + v[4 + k];
+                    for (int k = 0; k < 4; k++) {
+                        const T r0 = swp ? b[k] : a[k], r1 = swp ? a[k] : b[k];
+                        own[j][k] = own[j][k] + r0 + r1;
+                    }
                 } else {
                     // rows 2*P0 .. 2*P0+7 hold both inserted-bit rows of all four
-                    ld4(buf + 2 * P0, v);
-                    ld4(buf + 2 * P0 + 4, v + 4);
+                    T a[4], b[4];
+                    ld4(buf + 2 * P0 + (swp ? 4 : 0), a);
+                    ld4(buf + 2 * P0 + (swp ? 0 : 4), b);
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        v[k] = swp ? b[k] : a[k];
+                        v[4 + k] = swp ? a[k] : b[k];
+                    }
 #pragma unroll
                     for (int k = 0; k < 4; k++) {
                         if (P0 + k < row_lo) continue;
