@@ -439,10 +439,10 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
 // the same reductions in the working precision, sum and maximum together
 // (one shared-memory round trip; fixed tree, so deterministic); thread 0
 // gets the block's values.  red holds 2 * SW_THREADS / 32 elements.
-template <typename T>
+template <typename T, int NT = SW_THREADS>
 __device__ __forceinline__ void block_sum_max_t(T &s, T &m, T *red) {
     const unsigned FULL = 0xffffffffu;
-    constexpr int NW = SW_THREADS / 32;
+    constexpr int NW = NT / 32;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         s += __shfl_xor_sync(FULL, s, o);
@@ -544,13 +544,13 @@ __device__ __forceinline__ uint32_t swz_pos(uint32_t x1, uint32_t c, int lw, int
     return ((x1 << lw) | c) ^ (((x1 >> (n1 - sb)) & ((1u << sb) - 1u)) << lw);
 }
 
-template <typename T>
+template <typename T, int NT = SW_THREADS>
 __device__ __forceinline__ void stage_rev_D(T *buf, const T *Dz, int n, int n1, int n2, int lw, uint32_t col0,
                                             int sb) {
     const uint32_t ntop = (1u << n1) << lw, cm = (1u << lw) - 1u;
     const uint32_t full = (1u << n) - 1u;
 #pragma unroll 4
-    for (uint32_t idx = threadIdx.x; idx < ntop; idx += SW_THREADS) {
+    for (uint32_t idx = threadIdx.x; idx < ntop; idx += NT) {
         const uint32_t o = idx >> lw, c = idx & cm;
         uint32_t j = (rev_bits(col0 + c, n2) << n1) | o;
         if ((j >> (n2 - 1)) & 1u) j ^= full;  // held as its complement
@@ -1053,13 +1053,13 @@ __global__ void __launch_bounds__(SW_THREADS, tile_blocks<T>(R * SW_THREADS * si
 // all-shared-memory kernels.
 // ---------------------------------------------------------------------------
 
-template <typename T, int NL, bool HALF>
-__global__ void __launch_bounds__(SW_THREADS, tile_blocks<T>((size_t)SW_THREADS * (2 << NL) * sizeof(T), 2))
+template <typename T, int NL, bool HALF, int CT>
+__global__ void __launch_bounds__(CT, CT >= 1024 ? 1 : tile_blocks<T>((size_t)CT * (2 << NL) * sizeof(T), 2))
 k_cols_fwd_l(SweepArgs a, T *__restrict__ p, const T *__restrict__ D, T *__restrict__ F1, int apply_update,
              int sym_rev) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *buf = reinterpret_cast<T *>(smem_raw);
-    __shared__ T red[2 * SW_THREADS / 32];
+    __shared__ T red[2 * CT / 32];
     constexpr int NI = 1 << NL;
     const int z = blockIdx.y;
     const double *inst = a.inst + z * INST_STRIDE;
@@ -1074,7 +1074,7 @@ k_cols_fwd_l(SweepArgs a, T *__restrict__ p, const T *__restrict__ D, T *__restr
     const bool symr = HALF && sym_rev && upd && flag_set(inst, I_SYMNEED);
     const int sb = swz_bits(n1, lw);
     if (symr) {
-        stage_rev_D<T>(buf, Dz, a.n, n1, n2, lw, col0, sb);
+        stage_rev_D<T, CT>(buf, Dz, a.n, n1, n2, lw, col0, sb);
         __syncthreads();
     }
     // all of a thread's global loads are issued before its first store; input
@@ -1106,24 +1106,24 @@ k_cols_fwd_l(SweepArgs a, T *__restrict__ p, const T *__restrict__ D, T *__restr
     for (int r = 1; r < 2 * NI; r++) buf[((((uint32_t)r << L) | sigma) << lw) | c] = v[r];
     buf[(sigma << lw) | c] = (T)0;  // rows [0, 2^L) start the shared-memory steps at 0
     T pmax = (T)0;
-    block_sum_max_t<T>(psum, pmax, red);  // (its barrier also publishes the rows above)
+    block_sum_max_t<T, CT>(psum, pmax, red);  // (its barrier also publishes the rows above)
     if (threadIdx.x == 0) {
         double *pp = a.part + ((size_t)z * 2 + 0) * a.maxblk * 4 + blockIdx.x * 4;
         pp[0] = (double)psum * (HALF ? 2.0 : 1.0);  // each column also stands for its complement
     }
-    lsweep_fwd_any<T, NI>(buf, n1, lw, NL);
+    lsweep_fwd_any<T, NI, CT>(buf, n1, lw, NL);
     T *Fz = F1 + z * a.strideN;
     const uint32_t ntop = (1u << n1) << lw;
     if (lw >= 2) {
 #pragma unroll 4
-        for (uint32_t e = w + 4 * threadIdx.x; e < ntop; e += 4 * SW_THREADS) {
+        for (uint32_t e = w + 4 * threadIdx.x; e < ntop; e += 4 * CT) {
             uint32_t row = e >> lw, cc = e & (w - 1u);
             T t4[4];
             ld4(buf + e, t4);
             st4(Fz + (((size_t)row << n2) | (col0 + cc)), t4);
         }
     } else {
-        for (uint32_t e = threadIdx.x + w; e < ntop; e += SW_THREADS) {
+        for (uint32_t e = threadIdx.x + w; e < ntop; e += CT) {
             uint32_t row = e >> lw, cc = e & (w - 1u);
             Fz[((size_t)row << n2) | (col0 + cc)] = buf[e];
         }
@@ -1136,13 +1136,13 @@ k_cols_fwd_l(SweepArgs a, T *__restrict__ p, const T *__restrict__ D, T *__restr
 // unnormalised and its sum is tracked, so any s is exact) and the forward
 // columns pass of iteration t+1 runs on the updated inputs, writing F1.  D is
 // not stored.
-template <typename T, int NL, bool HALF, bool STEP>
-__global__ void __launch_bounds__(SW_THREADS, tile_blocks<T>((size_t)SW_THREADS * (2 << NL) * sizeof(T), 2))
+template <typename T, int NL, bool HALF, bool STEP, int CT>
+__global__ void __launch_bounds__(CT, CT >= 1024 ? 1 : tile_blocks<T>((size_t)CT * (2 << NL) * sizeof(T), 2))
 k_cols_adj_l(SweepArgs a, EpiArgs ep, const T *__restrict__ Gb, T *__restrict__ pw, T *__restrict__ F1) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *buf = reinterpret_cast<T *>(smem_raw);
-    __shared__ T red[2 * SW_THREADS / 32];
-    __shared__ T red2[2 * SW_THREADS / 32];
+    __shared__ T red[2 * CT / 32];
+    __shared__ T red2[2 * CT / 32];
     constexpr int NI = 1 << NL;
     const int z = blockIdx.y;
     if (!flag_set(a.inst + z * INST_STRIDE, I_ACTIVE)) return;
@@ -1153,7 +1153,7 @@ k_cols_adj_l(SweepArgs a, EpiArgs ep, const T *__restrict__ Gb, T *__restrict__ 
     const uint32_t full2 = (1u << n2) - 1u;
     if (lw >= 2) {
 #pragma unroll 16
-        for (uint32_t e = 4 * threadIdx.x; e < nall; e += 4 * SW_THREADS) {
+        for (uint32_t e = 4 * threadIdx.x; e < nall; e += 4 * CT) {
             uint32_t row = e >> lw, cc = e & (w - 1u);
             T t4[4] = {(T)0, (T)0, (T)0, (T)0};
             if (row) {
@@ -1169,7 +1169,7 @@ k_cols_adj_l(SweepArgs a, EpiArgs ep, const T *__restrict__ Gb, T *__restrict__ 
             st4(buf + e, t4);
         }
     } else {
-        for (uint32_t e = threadIdx.x; e < nall; e += SW_THREADS) {
+        for (uint32_t e = threadIdx.x; e < nall; e += CT) {
             uint32_t row = e >> lw, cc = e & (w - 1u);
             T t = (T)0;
             if (row) t = (!HALF || in_h1(row)) ? Gz[((size_t)row << n2) | (col0 + cc)]
@@ -1178,7 +1178,7 @@ k_cols_adj_l(SweepArgs a, EpiArgs ep, const T *__restrict__ Gb, T *__restrict__ 
         }
     }
     __syncthreads();
-    lsweep_adj_any<T, 2 * NI>(buf, n1, lw, NL);
+    lsweep_adj_any<T, 2 * NI, CT>(buf, n1, lw, NL);
     const uint32_t c = threadIdx.x & (w - 1u), sigma = threadIdx.x >> lw;
     T v[2 * NI];
     v[0] = (T)0;
@@ -1209,7 +1209,7 @@ k_cols_adj_l(SweepArgs a, EpiArgs ep, const T *__restrict__ Gb, T *__restrict__ 
     if constexpr (!STEP) {
 #pragma unroll
         for (int r = 0; r < NI; r++) Dz[x0 + r * xs] = v[r];
-        block_sum_max_t<T>(tZ, tM, red);
+        block_sum_max_t<T, CT>(tZ, tM, red);
         if (threadIdx.x == 0) {
             double *pp = a.part + ((size_t)z * 2 + 1) * a.maxblk * 4 + blockIdx.x * 4;
             pp[0] = (double)tZ * (HALF ? 2.0 : 1.0);  // each column also stands for its complement
@@ -1227,9 +1227,9 @@ k_cols_adj_l(SweepArgs a, EpiArgs ep, const T *__restrict__ Gb, T *__restrict__ 
         for (int r = 0; r < NI; r++) v[NI + r] = v[NI + r] * exp2_t<T>(v[r] - shift);
 #pragma unroll
         for (int r = 0; r < NI; r++) pz[x0 + r * xs] = v[NI + r];
-        block_sum_max_t<T>(tZ, tM, red);
+        block_sum_max_t<T, CT>(tZ, tM, red);
         T unused = (T)0;
-        block_sum_max_t<T>(tP, unused, red2);
+        block_sum_max_t<T, CT>(tP, unused, red2);
         if (threadIdx.x == 0) {
             double *pp = a.part + ((size_t)z * 2 + 1) * a.maxblk * 4 + blockIdx.x * 4;
             pp[0] = (double)tZ * (HALF ? 2.0 : 1.0);  // each column also stands for its complement
@@ -1244,19 +1244,19 @@ k_cols_adj_l(SweepArgs a, EpiArgs ep, const T *__restrict__ Gb, T *__restrict__ 
         for (int r = 1; r < 2 * NI; r++) buf[((((uint32_t)r << L) | sigma) << lw) | c] = v[r];
         buf[(sigma << lw) | c] = (T)0;  // rows [0, 2^L) start the shared-memory steps at 0
         __syncthreads();
-        lsweep_fwd_any<T, NI>(buf, n1, lw, NL);
+        lsweep_fwd_any<T, NI, CT>(buf, n1, lw, NL);
         T *Fz = F1 + z * a.strideN;
         const uint32_t ntop = (1u << n1) << lw;
         if (lw >= 2) {
 #pragma unroll 4
-            for (uint32_t e = w + 4 * threadIdx.x; e < ntop; e += 4 * SW_THREADS) {
+            for (uint32_t e = w + 4 * threadIdx.x; e < ntop; e += 4 * CT) {
                 uint32_t row = e >> lw, cc = e & (w - 1u);
                 T t4[4];
                 ld4(buf + e, t4);
                 st4(Fz + (((size_t)row << n2) | (col0 + cc)), t4);
             }
         } else {
-            for (uint32_t e = threadIdx.x + w; e < ntop; e += SW_THREADS) {
+            for (uint32_t e = threadIdx.x + w; e < ntop; e += CT) {
                 uint32_t row = e >> lw, cc = e & (w - 1u);
                 Fz[((size_t)row << n2) | (col0 + cc)] = buf[e];
             }
@@ -1396,6 +1396,13 @@ inline int r_of(size_t elems) {
         }                                                                       \
     } while (0)
 
+// run BODY with the compile-time constant CT equal to the runtime value ct (512 or 1024)
+#define SW_WITH_CT(ct, BODY)                                   \
+    do {                                                       \
+        if ((ct) == 1024) { constexpr int CT = 1024; BODY; }   \
+        else { constexpr int CT = 512; BODY; }                 \
+    } while (0)
+
 // run BODY with the compile-time constant LT equal to the runtime value lt (7..9)
 #define SW_WITH_LT(lt, BODY)                                \
     do {                                                    \
@@ -1459,9 +1466,12 @@ cudaError_t prepare_all(size_t cols_bytes, size_t rows_bytes) {
 #define PREP_ONE(RR) PREP_ONE_H(RR, false) PREP_ONE_H(RR, true)
     PREP_ONE(1) PREP_ONE(2) PREP_ONE(4) PREP_ONE(8) PREP_ONE(16) PREP_ONE(32) PREP_ONE(64)
 #define PREP_L(NL, H)                                                                        \
-    if (err == cudaSuccess) err = allow_smem(k_cols_fwd_l<T, NL, H>, cols_bytes);            \
-    if (err == cudaSuccess) err = allow_smem(k_cols_adj_l<T, NL, H, false>, cols_bytes);     \
-    if (err == cudaSuccess) err = allow_smem(k_cols_adj_l<T, NL, H, true>, cols_bytes);      \
+    if (err == cudaSuccess) err = allow_smem(k_cols_fwd_l<T, NL, H, 512>, cols_bytes);       \
+    if (err == cudaSuccess) err = allow_smem(k_cols_fwd_l<T, NL, H, 1024>, cols_bytes);      \
+    if (err == cudaSuccess) err = allow_smem(k_cols_adj_l<T, NL, H, false, 512>, cols_bytes); \
+    if (err == cudaSuccess) err = allow_smem(k_cols_adj_l<T, NL, H, true, 512>, cols_bytes);  \
+    if (err == cudaSuccess) err = allow_smem(k_cols_adj_l<T, NL, H, false, 1024>, cols_bytes); \
+    if (err == cudaSuccess) err = allow_smem(k_cols_adj_l<T, NL, H, true, 1024>, cols_bytes);  \
     if (err == cudaSuccess) err = allow_smem(k_rows_adj_l<T, NL, H, 9>, rows_bytes);
     PREP_L(3, false) PREP_L(3, true) PREP_L(4, false) PREP_L(4, true)
     if constexpr (sizeof(T) == 4) { PREP_L(5, false) PREP_L(5, true) }
@@ -1492,9 +1502,13 @@ bool half_possible(const Sched &s) { return s.n2 > 0 && s.lw < s.n2 && s.n1 >= 1
 // where they are off or do not apply.  A column tile must hold
 // SW_THREADS << NL inputs; a forward row tile runs NL = 5 (FP32) / 4 (FP64)
 // on 2^(n2 - NL) threads, an adjoint row tile NL = n2 - 9 on 512 threads.
+// threads of a register-step column CTA: 1024 where one tile fills an SM's
+// shared memory (one CTA per SM), else 512 (two CTAs per SM)
+template <typename T>
+static int ct_cols(const Sched &s) { return tile_bytes_cols<T>(s) > 112 * 1024 ? 1024 : 512; }
 template <typename T>
 static int nl_cols(const bdc_engine *e, const Sched &s, int bit) {
-    const int nl = s.n1 + s.lw - 9, nmax = sizeof(T) == 4 ? 5 : 4;
+    const int nl = s.n1 + s.lw - (ct_cols<T>(s) == 1024 ? 10 : 9), nmax = sizeof(T) == 4 ? 5 : 4;
     return ((e->opt.use_regsteps & bit) && s.n2 > 0 && nl >= 3 && nl <= nmax && nl <= s.n1) ? nl : 0;
 }
 template <typename T>
@@ -1524,14 +1538,15 @@ bdc_status sweep_forward(bdc_engine *e, PrecBuf<T> &b, const T *p_src, int apply
     dim3 g1(half ? s.nblk_cols / 2 : s.nblk_cols, e->nd);
     const int rc = r_of(((size_t)1 << s.n1) << s.lw);
     const int nlc = (mode == MODE_ITER) ? nl_cols<T>(e, s, 4) : 0;
+    const int ct = ct_cols<T>(s);
     if (!cols && s.n2 > 0) {
         // F1 is current (written by the previous stepped adjoint pass)
     } else if (nlc && half)
-        SW_WITH_NL(T, nlc, (k_cols_fwd_l<T, NL, true><<<g1, SW_THREADS, sm1, e->stream>>>(
-                               a, p, b.D, b.F1, apply_update, sym_rev ? 1 : 0)));
+        SW_WITH_CT(ct, SW_WITH_NL(T, nlc, (k_cols_fwd_l<T, NL, true, CT><<<g1, CT, sm1, e->stream>>>(
+                                              a, p, b.D, b.F1, apply_update, sym_rev ? 1 : 0))));
     else if (nlc)
-        SW_WITH_NL(T, nlc, (k_cols_fwd_l<T, NL, false><<<g1, SW_THREADS, sm1, e->stream>>>(
-                               a, p, b.D, b.F1, apply_update, 0)));
+        SW_WITH_CT(ct, SW_WITH_NL(T, nlc, (k_cols_fwd_l<T, NL, false, CT><<<g1, CT, sm1, e->stream>>>(
+                                              a, p, b.D, b.F1, apply_update, 0))));
     else if (half)
         SW_WITH_R(rmax_fwd<T>(), rc, (k_cols_fwd<T, R, true><<<g1, SW_THREADS, sm1, e->stream>>>(
                                          a, p, b.D, b.F1, b.q, b.L, apply_update, mode, sym_rev ? 1 : 0)));
@@ -1612,18 +1627,19 @@ bdc_status sweep_adjoint(bdc_engine *e, PrecBuf<T> &b, const T *Lsrc, const T *o
     dim3 g1(half ? s.nblk_cols / 2 : s.nblk_cols, e->nd);
     const int rc = r_of(((size_t)2 << s.n1) << s.lw);
     const int nlc = (mode == MODE_ITER) ? nl_cols<T>(e, s, 8) : 0;
+    const int ct = ct_cols<T>(s);
     if (step && nlc && half)
-        SW_WITH_NL(T, nlc, (k_cols_adj_l<T, NL, true, true><<<g1, SW_THREADS, sm1, e->stream>>>(a, ep, b.Gb, b.p,
-                                                                                                 b.F1)));
+        SW_WITH_CT(ct, SW_WITH_NL(T, nlc, (k_cols_adj_l<T, NL, true, true, CT><<<g1, CT, sm1, e->stream>>>(
+                                              a, ep, b.Gb, b.p, b.F1))));
     else if (step && nlc)
-        SW_WITH_NL(T, nlc, (k_cols_adj_l<T, NL, false, true><<<g1, SW_THREADS, sm1, e->stream>>>(a, ep, b.Gb, b.p,
-                                                                                                  b.F1)));
+        SW_WITH_CT(ct, SW_WITH_NL(T, nlc, (k_cols_adj_l<T, NL, false, true, CT><<<g1, CT, sm1, e->stream>>>(
+                                              a, ep, b.Gb, b.p, b.F1))));
     else if (nlc && half)
-        SW_WITH_NL(T, nlc, (k_cols_adj_l<T, NL, true, false><<<g1, SW_THREADS, sm1, e->stream>>>(a, ep, b.Gb,
-                                                                                                  nullptr, nullptr)));
+        SW_WITH_CT(ct, SW_WITH_NL(T, nlc, (k_cols_adj_l<T, NL, true, false, CT><<<g1, CT, sm1, e->stream>>>(
+                                              a, ep, b.Gb, nullptr, nullptr))));
     else if (nlc)
-        SW_WITH_NL(T, nlc, (k_cols_adj_l<T, NL, false, false><<<g1, SW_THREADS, sm1, e->stream>>>(a, ep, b.Gb,
-                                                                                                   nullptr, nullptr)));
+        SW_WITH_CT(ct, SW_WITH_NL(T, nlc, (k_cols_adj_l<T, NL, false, false, CT><<<g1, CT, sm1, e->stream>>>(
+                                              a, ep, b.Gb, nullptr, nullptr))));
     else if (half)
         SW_WITH_R(rmax_adj<T>(), rc,
                   (k_cols_adj<T, R, true><<<g1, SW_THREADS, sm1, e->stream>>>(a, ep, b.Gb, Lsrc, omega, mode)));
