@@ -75,7 +75,10 @@ def stage_bytes(n: int, n1: int, n2: int, elem: int, half: bool) -> dict:
 # (profiles/<kernel>_n24.md), keyed by stage, n and the (n1, n2, width)
 # schedule.  A kernel changed since its capture must be removed from here.
 MEASURED_TRAFFIC = {
-    ("rows_adj", 24, 11, 13, 4): 74.597888e6 + 34.273536e6,
+    ("cols_step", 24, 11, 13, 4): 135.171328e6 + 48.221696e6,
+    ("rows_adj", 24, 11, 13, 4): 74.511616e6 + 34.375168e6,
+    ("combine", 24, 11, 13, 4): 134.22848e6 + 29.461504e6,
+    ("rows_fwd", 24, 11, 13, 4): 67.136512e6 + 20.51584e6,
 }
 
 
@@ -455,26 +458,34 @@ def run_config(args):
             th = torch.tensor(theta0, dtype=torch.float64, device="cuda")
             (F, mD, g, gd), tg = _sync_time(lambda: eng.dual_bound(0, th, tau, "fp64", grad=True), stream)
             g = g.cpu().numpy()
-            errs, aerrs = [], []
+            errs, aerrs, top_errs = [], [], []
             gscale = float(np.max(np.abs(g)))
-            for i in inputs.fd_coordinates(len(theta0), 64, seed=0):
+
+            def fd_at(i):
                 tp, tm = th.clone(), th.clone()
                 tp[i] += h
                 tm[i] -= h
-                fd = (eng.dual_bound(0, tp, tau, "fp64", grad=False)[0] -
-                      eng.dual_bound(0, tm, tau, "fp64", grad=False)[0]) / (2 * h)
+                return (eng.dual_bound(0, tp, tau, "fp64", grad=False)[0] -
+                        eng.dual_bound(0, tm, tau, "fp64", grad=False)[0]) / (2 * h)
+
+            for i in inputs.fd_coordinates(len(theta0), 64, seed=0):
+                fd = fd_at(int(i))
                 aerrs.append(abs(fd - g[i]))
                 # relative error on the coordinates above 1e-3 of the largest: below
                 # that, the central difference's own rounding noise (~eps |F| / h
                 # = 1e-9) dominates; the absolute error covers every coordinate
                 if abs(g[i]) >= 1e-3 * gscale:
                     errs.append(abs(fd - g[i]) / abs(g[i]))
+            # the gradient sits on few output classes: relative error on the 8 largest
+            for i in np.argsort(-np.abs(g))[:8]:
+                top_errs.append(abs(fd_at(int(i)) - g[i]) / abs(g[i]))
             out, t = _sync_time(lambda: dual.optimize_dual(eng, 0, tau=tau, steps=200, lr=1e-2, ba_iters=0,
                                                            precision="fp32", theta0=theta0), stream)
             res.update({"n": n, "d": d, "tau": tau, "F": F, "max_D": mD, "dF_dd": gd,
                         "value_and_grad_ms_fp64": 1000 * tg, "fd_coords": len(aerrs), "fd_rel_coords": len(errs),
-                        "fd_max_rel_err": float(np.max(errs)), "fd_median_rel_err": float(np.median(errs)),
+                        "fd_max_rel_err": float(np.max(errs)) if errs else None,
                         "fd_max_abs_err": float(np.max(aerrs)), "grad_max_abs": gscale,
+                        "fd_top8_max_rel_err": float(np.max(top_errs)),
                         "ba_lower_after_50": float(eng.history(0)[0][-1]),
                         "adam_steps": 200, "adam_seconds": t,
                         "certified_initial": out["certified_initial"], "certified_final": out["certified_final"],

@@ -181,6 +181,13 @@ __global__ void k_clear_pending(int nd, double *inst) {
     if (z < nd) inst[z * INST_STRIDE + I_PENDING] = 0.0;
 }
 
+// a stepped sequence starts from shift 0, so that it depends on p alone (a
+// resumed checkpoint continues bit for bit)
+__global__ void k_reset_shift(int nd, double *inst) {
+    int z = blockIdx.x * blockDim.x + threadIdx.x;
+    if (z < nd) inst[z * INST_STRIDE + I_SHIFT] = 0.0;
+}
+
 __global__ void k_clear_symneed(int nd, double *inst) {
     int z = blockIdx.x * blockDim.x + threadIdx.x;
     if (z < nd) inst[z * INST_STRIDE + I_SYMNEED] = 0.0;
@@ -357,6 +364,12 @@ template <typename T>
 bdc_status launch_apply_pending(bdc_engine *e, PrecBuf<T> &b) {
     k_apply_pending<T><<<grid_for((size_t)1 << e->n, 256), 256, 0, e->stream>>>(e->n, e->nd, b.p, b.D, e->inst); e->launches++;
     k_clear_pending<<<(e->nd + 63) / 64, 64, 0, e->stream>>>(e->nd, e->inst); e->launches++;
+    BDC_CUDA_TRY(cudaGetLastError());
+    return BDC_OK;
+}
+
+bdc_status launch_reset_shift(bdc_engine *e) {
+    k_reset_shift<<<(e->nd + 63) / 64, 64, 0, e->stream>>>(e->nd, e->inst); e->launches++;
     BDC_CUDA_TRY(cudaGetLastError());
     return BDC_OK;
 }

@@ -204,6 +204,7 @@ bdc_status launch_literal_update(bdc_engine *e);
 bdc_status launch_literal_reduce(bdc_engine *e);
 bdc_status launch_clear_pending(bdc_engine *e);
 bdc_status launch_clear_symneed(bdc_engine *e);
+bdc_status launch_reset_shift(bdc_engine *e);
 bdc_status launch_finalize_literal(bdc_engine *e, int nblk0, int nblk1);
 bdc_status launch_expand_reps(bdc_engine *e, const double *Dr, double *out);
 int literal_grid(const bdc_engine *e);

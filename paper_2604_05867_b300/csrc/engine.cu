@@ -505,6 +505,7 @@ static bdc_status prime_step(bdc_engine *e, PrecBuf<T> &b, int prec, bool half) 
     BDC_TRY(sweep_forward<T>(e, b, b.p, 1, MODE_ITER, half, half && sym, true, false));
     BDC_TRY(launch_clear_pending(e));
     BDC_TRY(launch_clear_symneed(e));
+    BDC_TRY(launch_reset_shift(e));
     if (half) {
         e->half_active[prec] = true;
         e->half_n2[prec] = b.s.n2;

@@ -308,3 +308,69 @@ def test_prepared_graph_matches_stream_launches():
     assert np.array_equal(a.get_p(), b.get_p())
     a.close()
     b.close()
+
+
+def _stepped_engine(n, ds, **kw):
+    # n1 = n - 10, 32 columns: the register-step column kernels apply, so BA
+    # iterations run stepped (update and next forward columns pass in one kernel)
+    import paper_2604_05867_b300 as bdc
+    opts = dict(sched_n2_fp32=10, sched_w_fp32=32, sched_n2_fp64=10, sched_w_fp64=32)
+    opts.update(kw)
+    eng = bdc.Engine(n, ds, options=bdc.default_options(**opts))
+    assert _nl(eng.schedule("fp64"), "fp64")["cols"]
+    return eng
+
+
+def test_stepped_iterations_stop_at_the_first_small_gap():
+    # the stopping rule on the stepped path: an instance stops after the first
+    # iteration whose gap is below tol, and its iterations up to there are the
+    # same, bit for bit, as those of a run without a tolerance (graph replays
+    # of 3 iterations, so the stop falls inside a chunk)
+    n, d = 18, 0.5
+    ref = _stepped_engine(n, [d], chunk=3)
+    ref.iterate(40, -1.0, "fp64", "sweep")
+    lo_r, up_r = ref.history(0)
+    gaps = up_r - lo_r
+    tol = float(gaps[11]) * (1 + 1e-9)
+    stop = int(np.argmax(gaps < tol)) + 1  # first iteration with a gap below tol (at most 12)
+    eng = _stepped_engine(n, [d], chunk=3)
+    lo, up, it = eng.iterate(40, tol, "fp64", "sweep")
+    assert it[0] == stop
+    la, ua = eng.history(0)
+    assert np.array_equal(la, lo_r[:stop]) and np.array_equal(ua, up_r[:stop])
+    ref.close()
+    eng.close()
+
+
+def test_stepped_instances_are_independent():
+    n = 18
+    ds = [0.3, 0.8]
+    both = _stepped_engine(n, ds)
+    both.iterate(6, -1.0, "fp32", "sweep")
+    for z, d in enumerate(ds):
+        one = _stepped_engine(n, [d])
+        one.iterate(6, -1.0, "fp32", "sweep")
+        lb, ub = both.history(z)
+        lo, uo = one.history(0)
+        assert np.array_equal(lb, lo) and np.array_equal(ub, uo)
+        assert np.array_equal(both.get_p()[z], one.get_p()[0])
+        one.close()
+    both.close()
+
+
+def test_stepped_checkpoint_resume_is_bit_identical(tmp_path):
+    n, d = 18, 0.6
+    a = _stepped_engine(n, [d])
+    a.iterate(7, -1.0, "fp32", "sweep")
+    path = str(tmp_path / "ck_stepped.bin")
+    a.save(path)
+    a.iterate(9, -1.0, "fp32", "sweep")
+    b = _stepped_engine(n, [d])
+    b.load(path)
+    b.iterate(9, -1.0, "fp32", "sweep")
+    assert np.array_equal(a.get_p(), b.get_p())
+    la, ua = a.history(0)
+    lb, ub = b.history(0)
+    assert np.array_equal(la[-9:], lb[-9:]) and np.array_equal(ua[-9:], ub[-9:])
+    a.close()
+    b.close()
