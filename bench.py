@@ -75,8 +75,6 @@ def stage_bytes(n: int, n1: int, n2: int, elem: int, half: bool) -> dict:
 # (profiles/<kernel>_n24.md), keyed by stage, n and the (n1, n2, width)
 # schedule.  A kernel changed since its capture must be removed from here.
 MEASURED_TRAFFIC = {
-    ("cols_step", 24, 11, 13, 4): 135.171328e6 + 48.221696e6,
-    ("rows_adj", 24, 11, 13, 4): 74.511616e6 + 34.375168e6,
     ("combine", 24, 11, 13, 4): 134.22848e6 + 29.461504e6,
     ("rows_fwd", 24, 11, 13, 4): 67.136512e6 + 20.51584e6,
 }

@@ -274,20 +274,34 @@ __device__ void lsweep_adj_cols4(T *buf, int nn, int lw, int ie = 0) {
         uint32_t g = tid + j * NT;
         if (g < ng) ld4(buf + 4 * g, own[j]);
     }
-    for (int i = nn - 1; i >= ie; i--) {
-        const int m = nn - i - 1;
-        const uint32_t row_lo = 2u << m;
-        const uint32_t lomask = (1u << m) - 1u;
+    // steps m = 0 .. nn-1-ie, two per shared-memory round: with c = cmp_{m+1}(Q),
+    // G(m+2 done)[Q] = (G[Q] + G[cmp_m Q]) + (G[c] + G[cmp_m c]), the same
+    // additions in the same order as two single steps, half the barriers
+    const int mlast = nn - 1 - ie;
+    for (int m = 0; m <= mlast;) {
+        const bool two = m + 1 <= mlast;
+        const uint32_t row_lo = 2u << m, row_lo2 = 4u << m;
+        const uint32_t lomask = (1u << m) - 1u, lomask2 = (2u << m) - 1u;
 #pragma unroll
         for (int j = 0; j < G; j++) {
             uint32_t g = tid + j * NT;
-            uint32_t e = 4 * g, Q = e >> lw;
+            uint32_t e = 4 * g, Q = e >> lw, c = e & cmask;
             if (g < ng && Q >= row_lo) {
                 uint32_t cq = ((Q >> (m + 1)) << m) | (Q & lomask);
                 T a[4];
-                ld4(buf + ((cq << lw) | (e & cmask)), a);
+                ld4(buf + ((cq << lw) | c), a);
+                if (two && Q >= row_lo2) {
+                    uint32_t c1 = ((Q >> (m + 2)) << (m + 1)) | (Q & lomask2);
+                    uint32_t c1q = ((c1 >> (m + 1)) << m) | (c1 & lomask);
+                    T b[4], d[4];
+                    ld4(buf + ((c1 << lw) | c), b);
+                    ld4(buf + ((c1q << lw) | c), d);
 #pragma unroll
-                for (int k = 0; k < 4; k++) own[j][k] = own[j][k] + a[k];
+                    for (int k = 0; k < 4; k++) own[j][k] = (own[j][k] + a[k]) + (b[k] + d[k]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; k++) own[j][k] = own[j][k] + a[k];
+                }
             }
         }
         __syncthreads();
@@ -297,6 +311,7 @@ __device__ void lsweep_adj_cols4(T *buf, int nn, int lw, int ie = 0) {
             if (g < ng && ((4 * g) >> lw) >= row_lo) st4(buf + 4 * g, own[j]);
         }
         __syncthreads();
+        m += two ? 2 : 1;
     }
 }
 
@@ -311,10 +326,13 @@ __device__ void lsweep_adj_rows4(T *buf, int nn, int ie = 0) {
         uint32_t g = tid + j * NT;
         if (g < ng) ld4(buf + 4 * g, own[j]);
     }
-    for (int i = nn - 1; i >= ie; i--) {
-        const int m = nn - i - 1;
-        const uint32_t row_lo = 2u << m;
-        const uint32_t lomask = (1u << m) - 1u;
+    // two steps per shared-memory round where possible (see lsweep_adj_cols4);
+    // the pairs are (0,1), (2,3), ...
+    const int mlast = nn - 1 - ie;
+    for (int m = 0; m <= mlast;) {
+        const bool two = m + 1 <= mlast;
+        const uint32_t row_lo = 2u << m, row_lo2 = 4u << m;
+        const uint32_t lomask = (1u << m) - 1u, lomask2 = (2u << m) - 1u;
 #pragma unroll
         for (int j = 0; j < G; j++) {
             uint32_t g = tid + j * NT;
@@ -324,8 +342,32 @@ __device__ void lsweep_adj_rows4(T *buf, int nn, int ie = 0) {
                     uint32_t cq = ((Q0 >> (m + 1)) << m) | (Q0 & lomask);
                     T a[4];
                     ld4(buf + cq, a);
+                    if (two && Q0 >= row_lo2) {
+                        uint32_t c1 = ((Q0 >> (m + 2)) << (m + 1)) | (Q0 & lomask2);
+                        uint32_t c1q = ((c1 >> (m + 1)) << m) | (c1 & lomask);
+                        T b[4], d[4];
+                        ld4(buf + c1, b);
+                        ld4(buf + c1q, d);
 #pragma unroll
-                    for (int k = 0; k < 4; k++) own[j][k] = own[j][k] + a[k];
+                        for (int k = 0; k < 4; k++) own[j][k] = (own[j][k] + a[k]) + (b[k] + d[k]);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 4; k++) own[j][k] = own[j][k] + a[k];
+                    }
+                } else if (two) {
+                    // m == 0 and 1 together (only when m == 0): row 4g+k gets
+                    // (G[4g+k] + G[2g + (k>>1)]) + (G[2g + (k&1)] + G[g]) for g >= 1;
+                    // rows 2 and 3 get G[1] (step 0 only)
+                    T a[2];
+                    ld2(buf + 2 * g, a);
+                    if (g >= 1) {
+                        const T cg = buf[g];
+#pragma unroll
+                        for (int k = 0; k < 4; k++) own[j][k] = (own[j][k] + a[k >> 1]) + (a[k & 1] + cg);
+                    } else {
+                        own[j][2] = own[j][2] + a[1];
+                        own[j][3] = own[j][3] + a[1];
+                    }
                 } else {
                     // m == 1: cmp = 2g, 2g+1, 2g, 2g+1 ; m == 0: cmp = 2g, 2g, 2g+1, 2g+1
                     T a[2];
@@ -351,6 +393,7 @@ __device__ void lsweep_adj_rows4(T *buf, int nn, int ie = 0) {
             }
         }
         __syncthreads();
+        m += two ? 2 : 1;
     }
 }
 
