@@ -844,13 +844,18 @@ __global__ void __launch_bounds__(256) k_combine_k(SweepArgs a, const T *__restr
         const uint32_t cnt = (k == 0) ? 1u : (HALF ? 1u << (k - 1) : 1u << k);
         const uint32_t y0 = (blockIdx.x == 0) ? 0u : (blockIdx.x - (1u << (k - KB))) << CMB_LOG;
         const int jlo = max(0, k - n2), jhi = min(k, n1);
-#pragma unroll 4
-        for (int r = 0; r < CMB_CODES / 256; r++) {
-            const uint32_t y = y0 + r * 256 + threadIdx.x;
-            if (y >= cnt) break;
-            T acc = (T)0;
-            for (int j = jlo; j <= jhi; j++) {
-                const int l = k - j;
+        // the thread's CMB_CODES / 256 codes advance through the splits
+        // together: their loads of one split are independent and in flight at once
+        constexpr int RC = CMB_CODES / 256;
+        T acc[RC];
+#pragma unroll
+        for (int r = 0; r < RC; r++) acc[r] = (T)0;
+        for (int j = jlo; j <= jhi; j++) {
+            const int l = k - j;
+#pragma unroll
+            for (int r = 0; r < RC; r++) {
+                const uint32_t y = y0 + r * 256 + threadIdx.x;
+                if (y >= cnt) break;
                 uint32_t c1 = (1u << j) | (y >> l);
                 uint32_t u2 = y & ((1u << l) - 1u);
                 T v;
@@ -865,10 +870,16 @@ __global__ void __launch_bounds__(256) k_combine_k(SweepArgs a, const T *__restr
                 } else {
                     v = Tmz[((size_t)c1 << n2) + ((1u << l) | u2)];
                 }
-                acc += v;
+                acc[r] += v;
             }
+        }
+#pragma unroll
+        for (int r = 0; r < RC; r++) {
+            const uint32_t y = y0 + r * 256 + threadIdx.x;
+            if (y >= cnt) break;
+            const T accr = acc[r];
             const uint32_t c = (1u << k) | y;
-            T qv = acc * inv_binom_t<T>(a, k);
+            T qv = accr * inv_binom_t<T>(a, k);
             T lv = log2_t<T>(mode == MODE_CERT ? fmin(qv, (T)1) : fmax(qv, q_floor_t<T>(a)));
             if (keep_q) qz[c] = qv;
             Lz[c] = lv;
