@@ -43,41 +43,13 @@ __global__ void k_build_Hb(int n, int nd, const uint32_t *reps, int64_t R, const
     }
 }
 
-// one block per instance; partials reduced in a fixed order (deterministic).
-// stepped: the update was applied in the adjoint columns pass (which also
-// summed p into slot 1 [2]), so nothing is left pending
+// one block per instance; partials reduced in a fixed order (deterministic)
 __global__ void k_finalize_iter(int nd, const double *part, int maxblk, int nblk0, int nblk1, double *inst,
                                 double *hist, int stepped) {
     __shared__ double red[FIN_THREADS / 32];
     const int z = blockIdx.x;
-    double *I = inst + z * INST_STRIDE;
-    if (I[I_ACTIVE] == 0.0) return;
-    const double *p0 = part + ((size_t)z * 2 + 0) * maxblk * 4;
-    const double *p1 = part + ((size_t)z * 2 + 1) * maxblk * 4;
-    double Zp = stepped ? fin_sum(p1 + 2, 4, nblk1, red) : fin_sum(p0, 4, nblk0, red);
-    double ZD = fin_sum(p1, 4, nblk1, red);
-    double mD = fin_max(p1 + 1, 4, nblk1, red);
-    if (threadIdx.x != 0) return;
-    if (!isfinite(ZD) || !isfinite(mD) || !(Zp > 0.0) || !isfinite(Zp) || !(ZD > 0.0)) {
-        I[I_STATUS] = (double)BDC_ENONFINITE;
-        I[I_ACTIVE] = 0.0;
-        return;
-    }
-    double lower = log2(ZD);  // = log2 sum_x (p/Zp) 2^{D_x}, D_x = D_stored + log2 Zp
-    double upper = mD + log2(Zp);
-    I[I_LOWER] = lower;
-    I[I_UPPER] = upper;
-    I[I_ZP] = Zp;
-    I[I_MAXD] = mD;
-    I[I_SHIFT] = log2(ZD);
-    I[I_PENDING] = stepped ? 0.0 : 1.0;
-    I[I_SYMNEED] = stepped ? 0.0 : 1.0;
-    I[I_ITERS] += 1.0;
-    long h = (long)I[I_HISTN];
-    hist[((size_t)z * 2 + 0) * BDC_HIST + (h % BDC_HIST)] = lower;
-    hist[((size_t)z * 2 + 1) * BDC_HIST + (h % BDC_HIST)] = upper;
-    I[I_HISTN] = (double)(h + 1);
-    if (upper - lower < I[I_TOL]) I[I_ACTIVE] = 0.0;
+    if (inst[z * INST_STRIDE + I_ACTIVE] == 0.0) return;
+    finalize_instance<FIN_THREADS>(z, part, maxblk, nblk0, nblk1, inst, hist, stepped, red);
 }
 
 // sum of slot-0 partials -> inst[I_SUMP] = log2(sum)

@@ -256,33 +256,73 @@ __device__ __forceinline__ uint32_t orbit_rep_dev(uint32_t s, int L, int *osize)
     return m;
 }
 
-// Deterministic block reductions of block partials (blockDim.x = FIN_THREADS):
-// thread t folds elements t, t+FIN_THREADS, ... in order, then a fixed
-// shuffle tree and an in-order sum of the warp results.  Result in thread 0.
+// Deterministic block reductions of block partials (blockDim.x = NT): thread
+// t folds elements t, t+NT, ... in order, then a fixed shuffle tree and an
+// in-order sum of the warp results.  Result in thread 0.  Loads bypass L1:
+// the partials may come from other CTAs of the running kernel.
 constexpr int FIN_THREADS = 256;
+template <int NT = FIN_THREADS>
 __device__ __forceinline__ double fin_sum(const double *a, int stride, int count, double *red) {
     double s = 0.0;
-    for (int i = threadIdx.x; i < count; i += FIN_THREADS) s += a[(size_t)i * stride];
+    for (int i = threadIdx.x; i < count; i += NT) s += __ldcg(a + (size_t)i * stride);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     __syncthreads();
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
     __syncthreads();
     double t = 0.0;
     if (threadIdx.x == 0)
-        for (int w = 0; w < FIN_THREADS / 32; w++) t += red[w];
+        for (int w = 0; w < NT / 32; w++) t += red[w];
     return t;
 }
+template <int NT = FIN_THREADS>
 __device__ __forceinline__ double fin_max(const double *a, int stride, int count, double *red) {
     double s = -INFINITY;
-    for (int i = threadIdx.x; i < count; i += FIN_THREADS) s = fmax(s, a[(size_t)i * stride]);
+    for (int i = threadIdx.x; i < count; i += NT) s = fmax(s, __ldcg(a + (size_t)i * stride));
     for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
     __syncthreads();
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
     __syncthreads();
     double t = -INFINITY;
     if (threadIdx.x == 0)
-        for (int w = 0; w < FIN_THREADS / 32; w++) t = fmax(t, red[w]);
+        for (int w = 0; w < NT / 32; w++) t = fmax(t, red[w]);
     return t;
+}
+
+// End of a BA iteration for instance z (all NT threads of the block call it):
+// lower = log2 sum_x (p/Zp) 2^{D_x}, upper = max D + log2 Zp, the normaliser
+// of the next update, history, stopping test.  stepped: the update was
+// applied in the adjoint columns pass (which also summed p into slot 1 [2]),
+// so nothing is left pending.
+template <int NT>
+__device__ __forceinline__ void finalize_instance(int z, const double *part, int maxblk, int nblk0, int nblk1,
+                                                  double *inst, double *hist, int stepped, double *red) {
+    double *I = inst + z * INST_STRIDE;
+    const double *p0 = part + ((size_t)z * 2 + 0) * maxblk * 4;
+    const double *p1 = part + ((size_t)z * 2 + 1) * maxblk * 4;
+    double Zp = stepped ? fin_sum<NT>(p1 + 2, 4, nblk1, red) : fin_sum<NT>(p0, 4, nblk0, red);
+    double ZD = fin_sum<NT>(p1, 4, nblk1, red);
+    double mD = fin_max<NT>(p1 + 1, 4, nblk1, red);
+    if (threadIdx.x != 0) return;
+    if (!isfinite(ZD) || !isfinite(mD) || !(Zp > 0.0) || !isfinite(Zp) || !(ZD > 0.0)) {
+        I[I_STATUS] = (double)BDC_ENONFINITE;
+        I[I_ACTIVE] = 0.0;
+        return;
+    }
+    double lower = log2(ZD);  // D_x = D_stored + log2 Zp
+    double upper = mD + log2(Zp);
+    I[I_LOWER] = lower;
+    I[I_UPPER] = upper;
+    I[I_ZP] = Zp;
+    I[I_MAXD] = mD;
+    I[I_SHIFT] = log2(ZD);
+    I[I_PENDING] = stepped ? 0.0 : 1.0;
+    I[I_SYMNEED] = stepped ? 0.0 : 1.0;
+    I[I_ITERS] += 1.0;
+    long h = (long)I[I_HISTN];
+    hist[((size_t)z * 2 + 0) * BDC_HIST + (h % BDC_HIST)] = lower;
+    hist[((size_t)z * 2 + 1) * BDC_HIST + (h % BDC_HIST)] = upper;
+    I[I_HISTN] = (double)(h + 1);
+    if (upper - lower < I[I_TOL]) I[I_ACTIVE] = 0.0;
 }
 
 template <typename T>
