@@ -61,6 +61,19 @@ __device__ __forceinline__ void clog2c_fix(uint32_t c, const longlong2 *__restri
     if (accF >= FRAC_ONE) { accF -= FRAC_ONE; accI += 1; }
 }
 
+// The same value split for summing with 64-bit shared-memory atomics:
+// hi = I 2^24 + (F >> 38), lo = F mod 2^38 (units of 2^-62 overall).  Over at
+// most C(26,13) < 2^24 nodes of one length, sum hi < 2^53 and sum lo < 2^62, so
+// neither overflows and the sums are exact in any order.
+__device__ __forceinline__ void clog2c_parts(uint32_t c, const longlong2 *__restrict__ tab, unsigned long long &hi,
+                                             unsigned long long &lo) {
+    long long I = 0;
+    unsigned long long F = 0;
+    clog2c_fix(c, tab, I, F);
+    hi = ((unsigned long long)I << 24) + (F >> 38);
+    lo = F & ((1ull << 38) - 1ull);
+}
+
 // ---------------------------------------------------------------------------
 // orbit representatives of {0,1}^L (L = n for inputs) : is_rep flags counted
 // per block, scanned, then written in increasing order (deterministic).
@@ -199,6 +212,10 @@ struct WalkArgs {
 template <int MODE>
 __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) {
     __shared__ uint32_t stkE[WARPS_PER_CTA][STK][32];
+    // WALK_STATS: per warp and length, the exact sums of c*log2(c) (hi, lo parts);
+    // nodes are buffered 32 at a time (lane i holds the i-th) and folded in by
+    // all lanes at once
+    __shared__ unsigned long long wacc[MODE == WALK_STATS ? WARPS_PER_CTA : 1][BDC_MAXN + 1][2];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int n = a.n;
     const int z = blockIdx.y;  // instance (literal D)
@@ -208,6 +225,11 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
     const double *kw = (MODE == WALK_LITERAL_D) ? a.kw + z * (n + 1) : nullptr;
     const double *lkw = (MODE == WALK_LITERAL_D) ? a.lkw + z * (n + 1) : nullptr;
     const double *lb = (MODE == WALK_LITERAL_D) ? a.lb + z * (n + 1) : nullptr;
+    if (MODE == WALK_STATS && lane <= BDC_MAXN) {
+        wacc[wid][lane][0] = 0ull;
+        wacc[wid][lane][1] = 0ull;
+    }
+    __syncwarp();
     int64_t item = -1;
     int64_t static_next = (int64_t)blockIdx.x * WARPS_PER_CTA + wid;
     const int64_t static_stride = (int64_t)gridDim.x * WARPS_PER_CTA;
@@ -258,7 +280,17 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
             int k = bitlen32(code) - 1;
             // record (code, k, cnt)
             if (MODE == WALK_STATS) {
-                if (lane == k) { accN++; clog2c_fix(cnt, a.tabfix, accI, accF); }
+                if (lane == k) accN++;
+                if (lane == nbuf) { bcode = (uint32_t)k; bcnt = cnt; }
+                if (++nbuf == 32) {
+                    unsigned long long hi, lo;
+                    clog2c_parts(bcnt, a.tabfix, hi, lo);
+                    if (hi | lo) {
+                        atomicAdd(&wacc[wid][bcode][0], hi);
+                        atomicAdd(&wacc[wid][bcode][1], lo);
+                    }
+                    nbuf = 0;
+                }
             } else if (MODE == WALK_EMIT) {
                 if (lane == 0) a.emb[code] = cnt;
             } else {
@@ -288,11 +320,28 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
             }
         }
         if (MODE == WALK_STATS) {
+            if (lane < nbuf) {
+                unsigned long long hi, lo;
+                clog2c_parts(bcnt, a.tabfix, hi, lo);
+                if (hi | lo) {
+                    atomicAdd(&wacc[wid][bcode][0], hi);
+                    atomicAdd(&wacc[wid][bcode][1], lo);
+                }
+            }
+            __syncwarp();
             if (lane <= n) {
+                // total = hi 2^38 + lo in units of 2^-62: integer part and 62-bit fraction
+                const unsigned long long hi = wacc[wid][lane][0], lo = wacc[wid][lane][1];
+                const unsigned long long rest = ((hi & 0xffffffull) << 38) + lo;  // < 2^63
+                accI = (long long)(hi >> 24) + (long long)(rest >> 62);
+                accF = rest & (FRAC_ONE - 1ull);
+                wacc[wid][lane][0] = 0ull;
+                wacc[wid][lane][1] = 0ull;
                 if (a.Nk32) a.Nk32[item * a.stride + lane] = accN;
                 if (a.Nk64) a.Nk64[item * a.stride + lane] = accN;
                 if (a.Sk) a.Sk[item * a.stride + lane] = (double)accI + (double)accF * (1.0 / FRAC_SCALE);
             }
+            __syncwarp();
         } else if (MODE == WALK_LITERAL_D) {
             if (lane < nbuf) {
                 int kk = bitlen32(bcode) - 1;
