@@ -310,6 +310,25 @@ def run_ours(args, rank: int, world: int):
                 ms_lit = e0.elapsed_time(e1)
             eng.iterate(1, -1.0, "fp32", "sweep")  # back to the FP32 representation
 
+            # batched form at the same n: four d values in one engine (every launch
+            # covers all instances; the d-free precompute is shared)
+            ms_batch = None
+            if not args.skip_batched:
+                beng = bdc.Engine(n, [0.2, 0.4, 0.6, 0.8], options=bdc.default_options(enable_literal=0, chunk=8),
+                                  stream=stream)
+                beng.autotune("fp32", reps=3, cache=args.sched_cache)
+                beng.iterate(args.warmup, -1.0, "fp32", "sweep")
+                beng.prepare("fp32", "sweep")
+                torch.cuda.synchronize()
+                e0.record(stream)
+                beng.iterate(40, -1.0, "fp32", "sweep")
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms_batch = e0.elapsed_time(e1) / 40
+                beng.close()
+                del beng
+                torch.cuda.empty_cache()
+
             # end to end through the public API: one Engine.iterate(1) call per
             # step, bounds read back to the host every step
             K = max(10, min(args.steps, 50))
@@ -328,6 +347,8 @@ def run_ours(args, rank: int, world: int):
                     "fp64_literal_ms_per_iter": ms_lit,
                     "fp64_certify_ms": ms_cert,
                     "precompute_a0_s": a0_s,
+                    "batched_4d_ms_per_iter_all": ms_batch,
+                    "batched_4d_pair_evals_per_s": (4 * pairs_per_iteration(n) / (ms_batch / 1000.0)) if ms_batch else None,
                     "speedup_fp32_vs_fp64_sweep": ms64 / ms,
                     "speedup_fp32_sweep_vs_fp64_literal": (ms_lit / ms) if ms_lit else None,
                     "speedup_fp64_sweep_vs_fp64_literal": (ms_lit / ms64) if ms_lit else None,
@@ -525,6 +546,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-literal", action="store_true")
+    ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--config", default=None, choices=["ba10", "n20", "batched", "dual", "large"],
                     help="run one workload configuration end to end instead of the headline bench")
     ap.add_argument("--iters", type=int, default=0)
