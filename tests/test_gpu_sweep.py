@@ -125,3 +125,31 @@ def test_batched_instances_are_independent():
         fin = np.isfinite(D_ref)
         assert np.all(np.abs(D[z][fin] - D_ref[fin]) <= 1e-12 * np.maximum(1.0, np.abs(D_ref[fin])))
     eng.close()
+
+
+def test_full_size_bench_configuration():
+    # n = 24 in the headline bench's launch configuration (split 11 + 13, 4
+    # columns, half mode, register-resident and stepped iterations) against the
+    # unstepped, all-shared-memory, full-mode kernels; then sampled outputs and
+    # inputs of the resulting q and D against the oracle, one by one
+    n, d = 24, 0.5
+    sched = dict(sched_n2_fp32=13, sched_w_fp32=4, sched_n2_fp64=13, sched_w_fp64=4)
+    eng = _engine(n, [d], enable_literal=0, **sched)
+    assert (eng.schedule("fp32")["n1"], eng.schedule("fp32")["n2"]) == (11, 13)
+    eng.iterate(3, -1.0, "fp64", "sweep")
+    ref = _engine(n, [d], enable_literal=0, use_regsteps=0, fuse_update=0, use_half=0, **sched)
+    ref.iterate(3, -1.0, "fp64", "sweep")
+    la, ua = eng.history(0)
+    lb, ub = ref.history(0)
+    assert np.all(np.abs(la - lb) <= 1e-12 * np.abs(lb)) and np.all(np.abs(ua - ub) <= 1e-12 * np.abs(ub))
+    ref.close()
+    p = eng.get_p()[0]
+    q = eng.get_q("fp64")[0]
+    for c in [int((1 << 5) | 0b01101), int(inputs.random_codes(n, 1, seed=11)[0])]:
+        r = oracle.q_point(n, d, p, c)
+        assert abs(q[c] - r) <= 1e-12 * r
+    D = eng.divergence(precision="fp64").cpu().numpy()[0]
+    for x in inputs.random_inputs(n, 8, seed=12):
+        r = oracle.D_point(n, d, q, int(x))
+        assert abs(D[x] - r) <= 1e-11 * max(1.0, abs(r))
+    eng.close()
