@@ -26,6 +26,7 @@
 #include "bdc_internal.cuh"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace {
 
@@ -144,8 +145,14 @@ __device__ __forceinline__ void ld2(const double *p, double *v) {
 }
 
 // forward, tile of >= 4 columns (lw >= 2): group g = 4 columns of row (4g) >> lw
-template <typename T, int G, int NT = SW_THREADS>
-__device__ void lsweep_fwd_cols4(T *buf, int nn, int lw, int ib = 0) {
+// Final-output hook of the forward sweeps: with a callable `out`, the last
+// step's values are handed to out(g, v[4]) (g: the 4-element group) straight
+// from registers instead of being published to shared memory.
+struct NoOut {};
+
+template <typename T, int G, int NT = SW_THREADS, typename Out = NoOut>
+__device__ void lsweep_fwd_cols4(T *buf, int nn, int lw, int ib = 0, Out out = Out()) {
+    constexpr bool DIRECT = !std::is_same<Out, NoOut>::value;
     const int tid = threadIdx.x;
     const uint32_t ng = ((1u << nn) << lw) >> 2;
     const uint32_t cmask = (1u << lw) - 1u;
@@ -181,6 +188,7 @@ __device__ void lsweep_fwd_cols4(T *buf, int nn, int lw, int ib = 0) {
                 }
             }
         }
+        if (DIRECT && i == nn - 1) break;
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < G; j++) {
@@ -189,11 +197,19 @@ __device__ void lsweep_fwd_cols4(T *buf, int nn, int lw, int ib = 0) {
         }
         __syncthreads();
     }
+    if constexpr (DIRECT) {
+#pragma unroll
+        for (int j = 0; j < G; j++) {
+            uint32_t g = tid + j * NT;
+            if (g < ng) out(g, own[j]);
+        }
+    }
 }
 
 // forward, one-column tile (lw == 0): group g = rows 4g..4g+3 (nn >= 2)
-template <typename T, int G, int NT = SW_THREADS>
-__device__ void lsweep_fwd_rows4(T *buf, int nn, int ib = 0) {
+template <typename T, int G, int NT = SW_THREADS, typename Out = NoOut>
+__device__ void lsweep_fwd_rows4(T *buf, int nn, int ib = 0, Out out = Out()) {
+    constexpr bool DIRECT = !std::is_same<Out, NoOut>::value;
     const int tid = threadIdx.x;
     const uint32_t ng = (1u << nn) >> 2;
     T own[G][4];
@@ -246,6 +262,7 @@ __device__ void lsweep_fwd_rows4(T *buf, int nn, int ib = 0) {
                 }
             }
         }
+        if (DIRECT && i == nn - 1) break;
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < G; j++) {
@@ -260,7 +277,16 @@ __device__ void lsweep_fwd_rows4(T *buf, int nn, int ib = 0) {
         }
         __syncthreads();
     }
+    if constexpr (DIRECT) {
+#pragma unroll
+        for (int j = 0; j < G; j++) {
+            uint32_t g = tid + j * NT;
+            if (g < ng) out(g, own[j]);
+        }
+    }
 }
+
+
 
 // adjoint, tile of >= 4 columns
 template <typename T, int G, int NT = SW_THREADS>
@@ -399,13 +425,21 @@ __device__ void lsweep_adj_rows4(T *buf, int nn, int ie = 0) {
 
 // choose the form: R = elements per thread (power of two).  R >= 4 and a tile
 // of >= 4 columns or one column use the 4-wide forms; otherwise scalar.
-template <typename T, int R, int NT = SW_THREADS>
-__device__ __forceinline__ void lsweep_fwd_any(T *buf, int nn, int lw, int ib = 0) {
+template <typename T, int R, int NT = SW_THREADS, typename Out = NoOut>
+__device__ __forceinline__ void lsweep_fwd_any(T *buf, int nn, int lw, int ib = 0, Out out = Out()) {
     if constexpr (R >= 4) {
-        if (lw >= 2) { lsweep_fwd_cols4<T, R / 4, NT>(buf, nn, lw, ib); return; }
-        if (lw == 0 && nn >= 2) { lsweep_fwd_rows4<T, R / 4, NT>(buf, nn, ib); return; }
+        if (lw >= 2) { lsweep_fwd_cols4<T, R / 4, NT, Out>(buf, nn, lw, ib, out); return; }
+        if (lw == 0 && nn >= 2) { lsweep_fwd_rows4<T, R / 4, NT, Out>(buf, nn, ib, out); return; }
     }
     lsweep_fwd_reg<T, R, NT>(buf, nn, lw, ib);
+    if constexpr (!std::is_same<Out, NoOut>::value) {
+        // the scalar form publishes; hand the bottom half out from shared memory
+        for (uint32_t g = threadIdx.x; g < (((1u << nn) << lw) >> 2); g += NT) {
+            T v[4];
+            ld4(buf + 4 * g, v);
+            out(g, v);
+        }
+    }
 }
 
 template <typename T, int R, int NT = SW_THREADS>
@@ -1165,23 +1199,20 @@ k_cols_fwd_l(SweepArgs a, T *__restrict__ p, const T *__restrict__ D, T *__restr
         double *pp = a.part + ((size_t)z * 2 + 0) * a.maxblk * 4 + blockIdx.x * 4;
         pp[0] = (double)psum * (HALF ? 2.0 : 1.0);  // each column also stands for its complement
     }
-    lsweep_fwd_any<T, NI, CT>(buf, n1, lw, NL);
+    // the last step's values go straight to F1 (rows 1 .. 2^n1 - 1)
     T *Fz = F1 + z * a.strideN;
-    const uint32_t ntop = (1u << n1) << lw;
-    if (lw >= 2) {
-#pragma unroll 4
-        for (uint32_t e = w + 4 * threadIdx.x; e < ntop; e += 4 * CT) {
-            uint32_t row = e >> lw, cc = e & (w - 1u);
-            T t4[4];
-            ld4(buf + e, t4);
-            st4(Fz + (((size_t)row << n2) | (col0 + cc)), t4);
+    lsweep_fwd_any<T, NI, CT>(buf, n1, lw, NL, [&](uint32_t g, const T *v) {
+        const uint32_t e = 4 * g, row = e >> lw, cc = e & (w - 1u);
+        if (lw >= 2) {
+            if (row) st4(Fz + (((size_t)row << n2) | (col0 + cc)), v);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const uint32_t ek = e + k, rk = ek >> lw;
+                if (rk) Fz[((size_t)rk << n2) | (col0 + (ek & (w - 1u)))] = v[k];
+            }
         }
-    } else {
-        for (uint32_t e = threadIdx.x + w; e < ntop; e += CT) {
-            uint32_t row = e >> lw, cc = e & (w - 1u);
-            Fz[((size_t)row << n2) | (col0 + cc)] = buf[e];
-        }
-    }
+    });
 }
 
 // STEP: the iteration boundary in one pass over the tile.  After D and the
@@ -1298,29 +1329,28 @@ k_cols_adj_l(SweepArgs a, EpiArgs ep, const T *__restrict__ Gb, T *__restrict__ 
         for (int r = 1; r < 2 * NI; r++) buf[((((uint32_t)r << L) | sigma) << lw) | c] = v[r];
         buf[(sigma << lw) | c] = (T)0;  // rows [0, 2^L) start the shared-memory steps at 0
         __syncthreads();
-        lsweep_fwd_any<T, NI, CT>(buf, n1, lw, NL);
+        // the last step's values go straight to F1 (rows 1 .. 2^n1 - 1)
         T *Fz = F1 + z * a.strideN;
-        const uint32_t ntop = (1u << n1) << lw;
-        if (lw >= 2) {
-#pragma unroll 4
-            for (uint32_t e = w + 4 * threadIdx.x; e < ntop; e += 4 * CT) {
-                uint32_t row = e >> lw, cc = e & (w - 1u);
-                T t4[4];
-                ld4(buf + e, t4);
-                st4(Fz + (((size_t)row << n2) | (col0 + cc)), t4);
+        lsweep_fwd_any<T, NI, CT>(buf, n1, lw, NL, [&](uint32_t g, const T *v) {
+            const uint32_t e = 4 * g, row = e >> lw, cc = e & (w - 1u);
+            if (lw >= 2) {
+                if (row) st4(Fz + (((size_t)row << n2) | (col0 + cc)), v);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const uint32_t ek = e + k, rk = ek >> lw;
+                    if (rk) Fz[((size_t)rk << n2) | (col0 + (ek & (w - 1u)))] = v[k];
+                }
             }
-        } else {
-            for (uint32_t e = threadIdx.x + w; e < ntop; e += CT) {
-                uint32_t row = e >> lw, cc = e & (w - 1u);
-                Fz[((size_t)row << n2) | (col0 + cc)] = buf[e];
-            }
-        }
+        });
     }
 }
 
 // rows pass, one row c1 per CTA, 2^LT threads, thread = sigma (n2 = NL + LT)
 template <typename T, int NL, bool HALF, int LT>
-__global__ void __launch_bounds__(1 << LT) k_rows_fwd_l(SweepArgs a, const T *p, const T *F1, T *Tm, T *Ts) {
+// (register budget for 768 resident threads per SM: 85 registers a thread)
+__global__ void __launch_bounds__(1 << LT, LT <= 8 ? 768 / (1 << LT) : 1)
+k_rows_fwd_l(SweepArgs a, const T *p, const T *F1, T *Tm, T *Ts) {
     constexpr int ROW_THREADS = 1 << LT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *buf = reinterpret_cast<T *>(smem_raw);
@@ -1350,10 +1380,20 @@ __global__ void __launch_bounds__(1 << LT) k_rows_fwd_l(SweepArgs a, const T *p,
     for (int r = 1; r < 2 * NI; r++) buf[((uint32_t)r << L) | sigma] = v[r];
     buf[sigma] = (T)0;
     __syncthreads();
-    lsweep_fwd_any<T, NI, ROW_THREADS>(buf, n2, 0, NL);
+    // the last step's values go straight out: codes c2 < 32 to the transposed
+    // Ts, the others to Tm row c1 (16-byte stores)
     T *Tmz = Tm + z * a.strideM;
     T *Tsz = Ts + z * ((size_t)32 << (n1 + 1));
-    store_row_T<T, ROW_THREADS>(buf, Tmz, Tsz, c1, n1, n2);
+    lsweep_fwd_any<T, NI, ROW_THREADS>(buf, n2, 0, NL, [&](uint32_t g, const T *v) {
+        const uint32_t c2 = 4 * g;
+        if (c2 >= 32) {
+            st4(Tmz + ((size_t)c1 << n2) + c2, v);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                if (c2 + k >= 1) Tsz[((size_t)(c2 + k) << (n1 + 1)) + c1] = v[k];
+        }
+    });
 }
 
 template <typename T, int NL, bool HALF, int LT>
