@@ -374,3 +374,37 @@ def test_stepped_checkpoint_resume_is_bit_identical(tmp_path):
     assert np.array_equal(la[-9:], lb[-9:]) and np.array_equal(ua[-9:], ub[-9:])
     a.close()
     b.close()
+
+
+def test_stepped_instances_stop_independently():
+    # two instances with very different gaps: the first stops early inside a
+    # graph chunk while the second keeps iterating; each matches its own
+    # single-instance run bit for bit (iterations, history, final p)
+    n = 18
+    ds = [0.05, 0.6]
+    ref = [_stepped_engine(n, [d], chunk=4) for d in ds]
+    hist = []
+    for e in ref:
+        e.iterate(30, -1.0, "fp64", "sweep")
+        lo, up = e.history(0)
+        hist.append((lo, up))
+    gaps0 = hist[0][1] - hist[0][0]
+    tol = float(gaps0[5]) * (1 + 1e-9)
+    stop0 = int(np.argmax(gaps0 < tol)) + 1
+    gaps1 = hist[1][1] - hist[1][0]
+    stop1 = int(np.argmax(gaps1 < tol)) + 1 if np.any(gaps1 < tol) else 30
+    assert stop0 < stop1
+    both = _stepped_engine(n, ds, chunk=4)
+    lo, up, it = both.iterate(30, tol, "fp64", "sweep")
+    assert list(it) == [stop0, stop1]
+    for z, (stop, (lr, ur)) in enumerate(zip([stop0, stop1], hist)):
+        la, ua = both.history(z)
+        assert np.array_equal(la, lr[:stop]) and np.array_equal(ua, ur[:stop])
+    for z, (stop, e) in enumerate(zip([stop0, stop1], ref)):
+        one = _stepped_engine(n, [ds[z]], chunk=4)
+        one.iterate(stop, -1.0, "fp64", "sweep")
+        assert np.array_equal(both.get_p()[z], one.get_p()[0])
+        one.close()
+    for e in ref:
+        e.close()
+    both.close()
