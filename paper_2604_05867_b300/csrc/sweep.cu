@@ -170,6 +170,29 @@ __device__ void lsweep_fwd_cols4(T *buf, int nn, int lw, int ib = 0, Out out = O
         // in 4 bank groups twice over.  Lanes 4-7 of each phase then load the
         // i1 row first, which spreads both loads over all 8 bank groups.
         const bool spread = (32u >> lw) > row_lo;
+        // group j of a thread: row P0 + j DQ, the same columns; where 2^m
+        // divides DQ its inserted-bit rows move by 2 DQ, i.e. 8NT elements
+        const uint32_t DQ = (4u * NT) >> lw;
+        if (G * NT == (int)ng && (DQ & (row_lo - 1u)) == 0u) {
+            const uint32_t P0 = (4u * tid) >> lw, c0 = (4u * tid) & cmask;
+            const uint32_t i00 = ((P0 >> m) << (m + 1)) | (P0 & (row_lo - 1u));
+            const bool swp = spread && ((tid >> 2) & 1u);
+            const T *pa = buf + (((swp ? (i00 | row_lo) : i00) << lw) | c0);
+            const T *pb = buf + (((swp ? i00 : (i00 | row_lo)) << lw) | c0);
+#pragma unroll
+            for (int j = 0; j < G; j++) {
+                if (P0 + j * DQ >= row_lo) {
+                    T a[4], b[4];
+                    ld4(pa + j * 8 * NT, a);
+                    ld4(pb + j * 8 * NT, b);
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        const T r0 = swp ? b[k] : a[k], r1 = swp ? a[k] : b[k];
+                        own[j][k] = own[j][k] + r0 + r1;
+                    }
+                }
+            }
+        } else
 #pragma unroll
         for (int j = 0; j < G; j++) {
             uint32_t g = tid + j * NT;
@@ -221,6 +244,27 @@ __device__ void lsweep_fwd_rows4(T *buf, int nn, int ib = 0, Out out = Out()) {
     for (int i = ib; i < nn; i++) {
         const int m = nn - i - 1;
         const uint32_t row_lo = 1u << m;
+        if (G * NT == (int)ng && m >= 2 && ((4u * NT) & (row_lo - 1u)) == 0u) {
+            // group j holds rows 4(tid + j NT) ..: its inserted-bit rows move by
+            // 8NT per group (see lsweep_fwd_cols4)
+            const uint32_t P00 = 4u * tid;
+            const uint32_t i00 = ((P00 >> m) << (m + 1)) | (P00 & (row_lo - 1u));
+            const bool swp = ((tid >> 2) & 1u) && row_lo < 32u;
+            const T *pa = buf + (swp ? (i00 | row_lo) : i00), *pb = buf + (swp ? i00 : (i00 | row_lo));
+#pragma unroll
+            for (int j = 0; j < G; j++) {
+                if (P00 + j * 4 * NT >= row_lo) {
+                    T a[4], b[4];
+                    ld4(pa + j * 8 * NT, a);
+                    ld4(pb + j * 8 * NT, b);
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        const T r0 = swp ? b[k] : a[k], r1 = swp ? a[k] : b[k];
+                        own[j][k] = own[j][k] + r0 + r1;
+                    }
+                }
+            }
+        } else
 #pragma unroll
         for (int j = 0; j < G; j++) {
             uint32_t g = tid + j * NT;
@@ -303,30 +347,61 @@ __device__ void lsweep_adj_cols4(T *buf, int nn, int lw, int ie = 0) {
     // steps m = 0 .. nn-1-ie, two per shared-memory round: with c = cmp_{m+1}(Q),
     // G(m+2 done)[Q] = (G[Q] + G[cmp_m Q]) + (G[c] + G[cmp_m c]), the same
     // additions in the same order as two single steps, half the barriers
+    // group j of a thread: row Q0 + j DQ, the same column c.  Where 2^(m+2)
+    // divides DQ the partner rows move linearly with j (cmp_m(Q + DQ) =
+    // cmp_m(Q) + DQ/2), so their addresses are the first group's plus j times
+    // a constant: 2NT elements for cmp_m Q and c, NT for cmp_m c
+    const uint32_t DQ = (4u * NT) >> lw;
+    const uint32_t Q0 = (4u * tid) >> lw, c0 = (4u * tid) & cmask;
     const int mlast = nn - 1 - ie;
     for (int m = 0; m <= mlast;) {
         const bool two = m + 1 <= mlast;
         const uint32_t row_lo = 2u << m, row_lo2 = 4u << m;
         const uint32_t lomask = (1u << m) - 1u, lomask2 = (2u << m) - 1u;
+        if (G * NT == (int)ng && (DQ & (row_lo2 - 1u)) == 0u) {
+            const uint32_t cq0 = ((Q0 >> (m + 1)) << m) | (Q0 & lomask);
+            const uint32_t c10 = ((Q0 >> (m + 2)) << (m + 1)) | (Q0 & lomask2);
+            const uint32_t c1q0 = ((c10 >> (m + 1)) << m) | (c10 & lomask);
+            const T *pa = buf + ((cq0 << lw) | c0), *pb = buf + ((c10 << lw) | c0), *pd = buf + ((c1q0 << lw) | c0);
 #pragma unroll
-        for (int j = 0; j < G; j++) {
-            uint32_t g = tid + j * NT;
-            uint32_t e = 4 * g, Q = e >> lw, c = e & cmask;
-            if (g < ng && Q >= row_lo) {
-                uint32_t cq = ((Q >> (m + 1)) << m) | (Q & lomask);
-                T a[4];
-                ld4(buf + ((cq << lw) | c), a);
-                if (two && Q >= row_lo2) {
-                    uint32_t c1 = ((Q >> (m + 2)) << (m + 1)) | (Q & lomask2);
-                    uint32_t c1q = ((c1 >> (m + 1)) << m) | (c1 & lomask);
-                    T b[4], d[4];
-                    ld4(buf + ((c1 << lw) | c), b);
-                    ld4(buf + ((c1q << lw) | c), d);
+            for (int j = 0; j < G; j++) {
+                const uint32_t Q = Q0 + j * DQ;
+                if (Q >= row_lo) {
+                    T a[4];
+                    ld4(pa + j * 2 * NT, a);
+                    if (two && Q >= row_lo2) {
+                        T b[4], d[4];
+                        ld4(pb + j * 2 * NT, b);
+                        ld4(pd + j * NT, d);
 #pragma unroll
-                    for (int k = 0; k < 4; k++) own[j][k] = (own[j][k] + a[k]) + (b[k] + d[k]);
-                } else {
+                        for (int k = 0; k < 4; k++) own[j][k] = (own[j][k] + a[k]) + (b[k] + d[k]);
+                    } else {
 #pragma unroll
-                    for (int k = 0; k < 4; k++) own[j][k] = own[j][k] + a[k];
+                        for (int k = 0; k < 4; k++) own[j][k] = own[j][k] + a[k];
+                    }
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < G; j++) {
+                uint32_t g = tid + j * NT;
+                uint32_t e = 4 * g, Q = e >> lw, c = e & cmask;
+                if (g < ng && Q >= row_lo) {
+                    uint32_t cq = ((Q >> (m + 1)) << m) | (Q & lomask);
+                    T a[4];
+                    ld4(buf + ((cq << lw) | c), a);
+                    if (two && Q >= row_lo2) {
+                        uint32_t c1 = ((Q >> (m + 2)) << (m + 1)) | (Q & lomask2);
+                        uint32_t c1q = ((c1 >> (m + 1)) << m) | (c1 & lomask);
+                        T b[4], d[4];
+                        ld4(buf + ((c1 << lw) | c), b);
+                        ld4(buf + ((c1q << lw) | c), d);
+#pragma unroll
+                        for (int k = 0; k < 4; k++) own[j][k] = (own[j][k] + a[k]) + (b[k] + d[k]);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 4; k++) own[j][k] = own[j][k] + a[k];
+                    }
                 }
             }
         }
@@ -355,10 +430,37 @@ __device__ void lsweep_adj_rows4(T *buf, int nn, int ie = 0) {
     // two steps per shared-memory round where possible (see lsweep_adj_cols4);
     // the pairs are (0,1), (2,3), ...
     const int mlast = nn - 1 - ie;
+    const bool exact = G * NT == (int)ng;
     for (int m = 0; m <= mlast;) {
         const bool two = m + 1 <= mlast;
         const uint32_t row_lo = 2u << m, row_lo2 = 4u << m;
         const uint32_t lomask = (1u << m) - 1u, lomask2 = (2u << m) - 1u;
+        if (exact && m >= 2 && ((4u * NT) & (row_lo2 - 1u)) == 0u) {
+            // group j holds rows 4(tid + j NT) ..: partner addresses move by
+            // 2NT (cmp_m Q, c) and NT (cmp_m c) per group (see lsweep_adj_cols4)
+            const uint32_t Q00 = 4u * tid;
+            const uint32_t cq0 = ((Q00 >> (m + 1)) << m) | (Q00 & lomask);
+            const uint32_t c10 = ((Q00 >> (m + 2)) << (m + 1)) | (Q00 & lomask2);
+            const uint32_t c1q0 = ((c10 >> (m + 1)) << m) | (c10 & lomask);
+#pragma unroll
+            for (int j = 0; j < G; j++) {
+                const uint32_t Q0 = Q00 + j * 4 * NT;
+                if (Q0 >= row_lo) {
+                    T a[4];
+                    ld4(buf + cq0 + j * 2 * NT, a);
+                    if (two && Q0 >= row_lo2) {
+                        T b[4], d[4];
+                        ld4(buf + c10 + j * 2 * NT, b);
+                        ld4(buf + c1q0 + j * NT, d);
+#pragma unroll
+                        for (int k = 0; k < 4; k++) own[j][k] = (own[j][k] + a[k]) + (b[k] + d[k]);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 4; k++) own[j][k] = own[j][k] + a[k];
+                    }
+                }
+            }
+        } else
 #pragma unroll
         for (int j = 0; j < G; j++) {
             uint32_t g = tid + j * NT;
