@@ -1293,8 +1293,10 @@ k_cols_fwd_l(SweepArgs a, T *__restrict__ p, const T *__restrict__ D, T *__restr
     if (symr) __syncthreads();  // every staged value is read: the rows are reused below
     local_fwd<T, NL>(v);
 #pragma unroll
-    for (int r = 1; r < 2 * NI; r++) buf[((((uint32_t)r << L) | sigma) << lw) | c] = v[r];
-    buf[(sigma << lw) | c] = (T)0;  // rows [0, 2^L) start the shared-memory steps at 0
+    // row (r << L) | sigma, column c sits at r * CT + threadIdx.x (2^L w = CT)
+#pragma unroll
+    for (int r = 1; r < 2 * NI; r++) buf[r * CT + threadIdx.x] = v[r];
+    buf[threadIdx.x] = (T)0;  // rows [0, 2^L) start the shared-memory steps at 0
     T pmax = (T)0;
     block_sum_max_t<T, CT>(psum, pmax, red);  // (its barrier also publishes the rows above)
     if (threadIdx.x == 0) {
@@ -1370,7 +1372,7 @@ k_cols_adj_l(SweepArgs a, EpiArgs ep, const T *__restrict__ Gb, T *__restrict__ 
     T v[2 * NI];
     v[0] = (T)0;
 #pragma unroll
-    for (int r = 1; r < 2 * NI; r++) v[r] = buf[((((uint32_t)r << L) | sigma) << lw) | c];
+    for (int r = 1; r < 2 * NI; r++) v[r] = buf[r * CT + threadIdx.x];  // row (r << L) | sigma, column c
     local_adj<T, NL>(v);
     const T *__restrict__ Hbz = reinterpret_cast<const T *>(ep.Hb) + z * a.strideN;
     // (STEP reads and rewrites p through this one pointer)
@@ -1428,8 +1430,8 @@ k_cols_adj_l(SweepArgs a, EpiArgs ep, const T *__restrict__ Gb, T *__restrict__ 
         local_fwd<T, NL>(v);
         __syncthreads();  // every thread has read its adjoint rows from buf
 #pragma unroll
-        for (int r = 1; r < 2 * NI; r++) buf[((((uint32_t)r << L) | sigma) << lw) | c] = v[r];
-        buf[(sigma << lw) | c] = (T)0;  // rows [0, 2^L) start the shared-memory steps at 0
+        for (int r = 1; r < 2 * NI; r++) buf[r * CT + threadIdx.x] = v[r];  // row (r << L) | sigma, column c
+        buf[threadIdx.x] = (T)0;  // rows [0, 2^L) start the shared-memory steps at 0
         __syncthreads();
         // the last step's values go straight to F1 (rows 1 .. 2^n1 - 1)
         T *Fz = F1 + z * a.strideN;
@@ -1459,7 +1461,7 @@ k_rows_fwd_l(SweepArgs a, const T *p, const T *F1, T *Tm, T *Ts) {
     constexpr int NI = 1 << NL;
     const int z = blockIdx.y;
     if (!flag_set(a.inst + z * INST_STRIDE, I_ACTIVE)) return;
-    const int n1 = a.n1, n2 = a.n2, L = n2 - NL;
+    const int n1 = a.n1, n2 = a.n2;  // n2 = NL + LT
     const uint32_t c1 = HALF ? half_row(blockIdx.x) : blockIdx.x + 1;
     const uint32_t half = 1u << n2, sigma = threadIdx.x;
     const T *src = (c1 >= (1u << n1)) ? p + z * a.strideN + ((size_t)(c1 - (1u << n1)) << n2)
@@ -1474,12 +1476,12 @@ k_rows_fwd_l(SweepArgs a, const T *p, const T *F1, T *Tm, T *Ts) {
     T v[2 * NI];
 #pragma unroll
     for (int r = 0; r < NI; r++) {
-        const uint32_t x2 = ((uint32_t)r << L) | sigma;
+        const uint32_t x2 = ((uint32_t)r << LT) | sigma;  // (L == LT)
         v[NI + r] = (HALF && x2 >= (half >> 1)) ? srcm[half - 1u - x2] : src[x2];
     }
     local_fwd<T, NL>(v);
 #pragma unroll
-    for (int r = 1; r < 2 * NI; r++) buf[((uint32_t)r << L) | sigma] = v[r];
+    for (int r = 1; r < 2 * NI; r++) buf[(r << LT) | sigma] = v[r];  // (L == LT)
     buf[sigma] = (T)0;
     __syncthreads();
     // the last step's values go straight out: codes c2 < 32 to the transposed
@@ -1506,7 +1508,7 @@ __global__ void __launch_bounds__(1 << LT) k_rows_adj_l(SweepArgs a, const T *Ls
     constexpr int NI = 1 << NL;
     const int z = blockIdx.y;
     if (!flag_set(a.inst + z * INST_STRIDE, I_ACTIVE)) return;
-    const int n2 = a.n2, n = a.n, L = n2 - NL;
+    const int n2 = a.n2, n = a.n;  // n2 = NL + LT
     const uint32_t c1 = HALF ? half_row(blockIdx.x) : blockIdx.x + 1;
     const int j = bitlen32(c1) - 1;
     gather_row_L<T, ROW_THREADS>(buf, Lsrc + z * a.strideM, omega + z * (n + 1), c1, j, n2);
@@ -1516,11 +1518,11 @@ __global__ void __launch_bounds__(1 << LT) k_rows_adj_l(SweepArgs a, const T *Ls
     T v[2 * NI];
     v[0] = (T)0;
 #pragma unroll
-    for (int r = 1; r < 2 * NI; r++) v[r] = buf[((uint32_t)r << L) | sigma];
+    for (int r = 1; r < 2 * NI; r++) v[r] = buf[(r << LT) | sigma];  // (L == LT)
     local_adj<T, NL>(v);
     T *Gz = Gb + z * a.strideM + ((size_t)c1 << n2);
 #pragma unroll
-    for (int r = 0; r < NI; r++) Gz[((uint32_t)r << L) | sigma] = v[NI + r];
+    for (int r = 0; r < NI; r++) Gz[(r << LT) | sigma] = v[NI + r];
 }
 
 template <typename T>
