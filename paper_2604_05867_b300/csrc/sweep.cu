@@ -1341,7 +1341,7 @@ k_cols_adj_l(SweepArgs a, EpiArgs ep, const T *__restrict__ Gb, T *__restrict__ 
     const T *Gz = Gb + z * a.strideM;
     const uint32_t full2 = (1u << n2) - 1u;
     if (lw >= 2) {
-#pragma unroll 8
+#pragma unroll 4
         for (uint32_t e = 4 * threadIdx.x; e < nall; e += 4 * CT) {
             uint32_t row = e >> lw, cc = e & (w - 1u);
             T t4[4] = {(T)0, (T)0, (T)0, (T)0};
