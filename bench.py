@@ -75,7 +75,6 @@ def stage_bytes(n: int, n1: int, n2: int, elem: int, half: bool) -> dict:
 # (profiles/<kernel>_n24.md), keyed by stage, n and the (n1, n2, width)
 # schedule.  A kernel changed since its capture must be removed from here.
 MEASURED_TRAFFIC = {
-    ("combine", 24, 11, 13, 4): 134.229504e6 + 27.213568e6,
 }
 
 

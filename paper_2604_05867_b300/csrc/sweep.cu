@@ -988,6 +988,28 @@ __global__ void __launch_bounds__(256) k_combine_k(SweepArgs a, const T *__restr
         for (int r = 0; r < RC; r++) acc[r] = (T)0;
         for (int j = jlo; j <= jhi; j++) {
             const int l = k - j;
+            if (blockIdx.x > 0 && l >= CMB_LOG) {
+                // the CTA's codes share y >> l (y0 is a multiple of 2^CMB_LOG):
+                // the term of code y0 + t is src[+-t] for one base per CTA
+                const uint32_t u20 = y0 & ((1u << l) - 1u);
+                uint32_t c1 = (1u << j) | (y0 >> l);
+                const T *src;
+                int sgn = 1;
+                if (l == n2) {
+                    uint32_t u2b = u20;
+                    if (HALF && u20 >= hh) {  // complement column of the complement row
+                        c1 = c1 ^ ((1u << j) - 1u);
+                        u2b = full2 - u20;
+                        sgn = -1;
+                    }
+                    src = ((j == n1) ? pz + ((size_t)(c1 ^ (1u << n1)) << n2) : Fz + ((size_t)c1 << n2)) + u2b;
+                } else {
+                    src = Tmz + ((size_t)c1 << n2) + (1u << l) + u20;
+                }
+#pragma unroll
+                for (int r = 0; r < RC; r++) acc[r] += src[sgn * (int)(r * 256 + threadIdx.x)];
+                continue;
+            }
 #pragma unroll
             for (int r = 0; r < RC; r++) {
                 const uint32_t y = y0 + r * 256 + threadIdx.x;
