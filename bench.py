@@ -75,6 +75,10 @@ def stage_bytes(n: int, n1: int, n2: int, elem: int, half: bool) -> dict:
 # (profiles/<kernel>_n24.md), keyed by stage, n and the (n1, n2, width)
 # schedule.  A kernel changed since its capture must be removed from here.
 MEASURED_TRAFFIC = {
+    ("cols_step", 24, 11, 13, 8): 134.299648e6 + 35.067904e6,
+    ("rows_adj", 24, 11, 13, 8): 74.451968e6 + 34.76608e6,
+    ("combine", 24, 11, 13, 8): 134.217216e6 + 27.237888e6,
+    ("rows_fwd", 24, 11, 13, 8): 67.13216e6 + 20.443392e6,
 }
 
 
