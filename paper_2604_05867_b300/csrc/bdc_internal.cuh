@@ -181,7 +181,7 @@ bdc_status sweep_forward(bdc_engine *e, PrecBuf<T> &b, const T *p_src, int apply
                          bool sym_rev = false, bool cols = true, bool rest = true);
 template <typename T>
 bdc_status sweep_adjoint(bdc_engine *e, PrecBuf<T> &b, const T *Lsrc, const T *omega, T *Dout, int mode,
-                         bool half = false, bool step = false);
+                         bool half = false, bool step = false, bool keep_p = true);
 bool half_possible(const Sched &s);
 // the adjoint columns pass can carry the BA update and the next forward
 // columns pass (register-resident column kernels apply)

@@ -1158,13 +1158,15 @@ static bdc_status time_sweeps(bdc_engine *e, PrecBuf<T> &b, int reps, float *ms)
     BDC_CUDA_TRY(cudaEventCreate(&z));
     bdc_status st = BDC_OK;
     // one untimed pass (first touch), then `reps` timed forward + adjoint sweeps
-    // as a BA iteration runs them (complement half mode where it applies); no
-    // update is applied, D is overwritten (the caller materialised p first)
+    // as a BA iteration runs them (complement half mode where it applies; the
+    // stepped columns pass where it applies, without storing its update); p is
+    // left as it was, D and F1 are overwritten (the caller materialised p first)
     const bool half = e->opt.use_half && e->half_ok && half_possible(b.s);
+    const bool stepped = step_possible<T>(e, b.s);
     for (int r = 0; r <= reps && st == BDC_OK; r++) {
         if (r == 1) cudaEventRecord(a, e->stream);
-        st = sweep_forward<T>(e, b, b.p, 0, MODE_ITER, half);
-        if (st == BDC_OK) st = sweep_adjoint<T>(e, b, b.L, b.omega, b.D, MODE_ITER, half);
+        st = sweep_forward<T>(e, b, b.p, 0, MODE_ITER, half, false, !stepped || r == 0);
+        if (st == BDC_OK) st = sweep_adjoint<T>(e, b, b.L, b.omega, b.D, MODE_ITER, half, stepped, false);
     }
     cudaEventRecord(z, e->stream);
     cudaError_t err = cudaEventSynchronize(z);

@@ -1349,7 +1349,8 @@ k_cols_fwd_l(SweepArgs a, T *__restrict__ p, const T *__restrict__ D, T *__restr
 // not stored.
 template <typename T, int NL, bool HALF, bool STEP, int CT>
 __global__ void __launch_bounds__(CT, CT >= 1024 ? 1 : tile_blocks<T>((size_t)CT * (2 << NL) * sizeof(T), 2))
-k_cols_adj_l(SweepArgs a, EpiArgs ep, const T *__restrict__ Gb, T *__restrict__ pw, T *__restrict__ F1) {
+k_cols_adj_l(SweepArgs a, EpiArgs ep, const T *__restrict__ Gb, T *__restrict__ pw, T *__restrict__ F1,
+             int keep_p = 1) {  // keep_p = 0: the updated p is not stored (schedule timing)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *buf = reinterpret_cast<T *>(smem_raw);
     __shared__ T red[2 * CT / 32];
@@ -1437,7 +1438,8 @@ k_cols_adj_l(SweepArgs a, EpiArgs ep, const T *__restrict__ Gb, T *__restrict__ 
 #pragma unroll
         for (int r = 0; r < NI; r++) v[NI + r] = v[NI + r] * exp2_t<T>(v[r] - shift);
 #pragma unroll
-        for (int r = 0; r < NI; r++) pz[x0 + r * xs] = v[NI + r];
+        for (int r = 0; r < NI; r++)
+            if (keep_p) pz[x0 + r * xs] = v[NI + r];
         block_sum_max_t<T, CT>(tZ, tM, red);
         T unused = (T)0;
         block_sum_max_t<T, CT>(tP, unused, red2);
@@ -1810,7 +1812,7 @@ bdc_status sweep_forward(bdc_engine *e, PrecBuf<T> &b, const T *p_src, int apply
 
 template <typename T>
 bdc_status sweep_adjoint(bdc_engine *e, PrecBuf<T> &b, const T *Lsrc, const T *omega, T *Dout, int mode, bool half,
-                         bool step) {
+                         bool step, bool keep_p) {
     SweepArgs a = make_args(e, b);
     const Sched &s = b.s;
     half = half && half_possible(s);
@@ -1850,10 +1852,10 @@ bdc_status sweep_adjoint(bdc_engine *e, PrecBuf<T> &b, const T *Lsrc, const T *o
     const int ct = ct_cols<T>(s);
     if (step && nlc && half)
         SW_WITH_CT(ct, SW_WITH_NL(T, nlc, (k_cols_adj_l<T, NL, true, true, CT><<<g1, CT, sm1, e->stream>>>(
-                                              a, ep, b.Gb, b.p, b.F1))));
+                                              a, ep, b.Gb, b.p, b.F1, keep_p ? 1 : 0))));
     else if (step && nlc)
         SW_WITH_CT(ct, SW_WITH_NL(T, nlc, (k_cols_adj_l<T, NL, false, true, CT><<<g1, CT, sm1, e->stream>>>(
-                                              a, ep, b.Gb, b.p, b.F1))));
+                                              a, ep, b.Gb, b.p, b.F1, keep_p ? 1 : 0))));
     else if (nlc && half)
         SW_WITH_CT(ct, SW_WITH_NL(T, nlc, (k_cols_adj_l<T, NL, true, false, CT><<<g1, CT, sm1, e->stream>>>(
                                               a, ep, b.Gb, nullptr, nullptr))));
@@ -1878,9 +1880,9 @@ template bdc_status sweep_forward<float>(bdc_engine *, PrecBuf<float> &, const f
 template bdc_status sweep_forward<double>(bdc_engine *, PrecBuf<double> &, const double *, int, int, bool, bool, bool,
                                           bool);
 template bdc_status sweep_adjoint<float>(bdc_engine *, PrecBuf<float> &, const float *, const float *, float *, int, bool,
-                                         bool);
+                                         bool, bool);
 template bdc_status sweep_adjoint<double>(bdc_engine *, PrecBuf<double> &, const double *, const double *, double *, int,
-                                          bool, bool);
+                                          bool, bool, bool);
 template bool step_possible<float>(const bdc_engine *, const Sched &);
 template bool step_possible<double>(const bdc_engine *, const Sched &);
 
