@@ -75,10 +75,6 @@ def stage_bytes(n: int, n1: int, n2: int, elem: int, half: bool) -> dict:
 # (profiles/<kernel>_n24.md), keyed by stage, n and the (n1, n2, width)
 # schedule.  A kernel changed since its capture must be removed from here.
 MEASURED_TRAFFIC = {
-    ("cols_step", 24, 11, 13, 8): 134.299648e6 + 35.067904e6,
-    ("rows_adj", 24, 11, 13, 8): 74.451968e6 + 34.76608e6,
-    ("combine", 24, 11, 13, 8): 134.217216e6 + 27.237888e6,
-    ("rows_fwd", 24, 11, 13, 8): 67.13216e6 + 20.443392e6,
 }
 
 
@@ -232,7 +228,11 @@ def run_ours(args, rank: int, world: int):
         eng = bdc.Engine(n, [d], options=bdc.default_options(enable_literal=1, chunk=8), stream=stream)
         a0_s = time.perf_counter() - t0
         # pick the sweep schedules for this GPU (part of the setup, not of a step)
-        sched32 = eng.autotune("fp32", reps=3, cache=args.sched_cache)
+        if args.sched_fp32:
+            n2s, ws = (int(v) for v in args.sched_fp32.split(","))
+            sched32 = dict(eng.set_schedule("fp32", n2s, ws), forced=True)
+        else:
+            sched32 = eng.autotune("fp32", reps=3, cache=args.sched_cache)
         sched64 = eng.autotune("fp64", reps=2, cache=args.sched_cache)
 
         # warm-up: W untimed FP32 iterations; the CUDA graph the timed call
@@ -550,6 +550,8 @@ def main():
     ap.add_argument("--config", default=None, choices=["ba10", "n20", "batched", "dual", "large"],
                     help="run one workload configuration end to end instead of the headline bench")
     ap.add_argument("--iters", type=int, default=0)
+    ap.add_argument("--sched-fp32", default=None, metavar="N2,W",
+                    help="use this FP32 sweep schedule (n2, column width) instead of the autotuner's")
     ap.add_argument("--sched-cache", default=None,
                     help="JSON file of tuned sweep schedules (read if present, written after a search)")
     ap.add_argument("--oracle-check", action="store_true")

@@ -188,6 +188,14 @@ class Engine:
         _check(lib().bdc_get_schedule(self._h, _PREC[precision], ctypes.byref(n1), ctypes.byref(n2), ctypes.byref(w)))
         return {"n1": n1.value, "n2": n2.value, "width": w.value}
 
+    def set_schedule(self, precision="fp32", n2: int = 13, width: int = 4):
+        """Use the sweep schedule (n1 = n - n2, n2, column tile width) instead of
+        searching (bdc_autotune with n2 > 0); raises on a schedule outside the
+        reserved buffers."""
+        ms = ctypes.c_double(0)
+        _check(lib().bdc_autotune(self._h, _PREC[precision], 1, int(n2), int(width), ctypes.byref(ms)))
+        return self.schedule(precision)
+
     def autotune(self, precision="fp32", reps: int = 3, cache: Optional[str] = None):
         """Pick the fastest sweep schedule for this engine (bdc_autotune).  With
         `cache` (a JSON file path) a result stored for this GPU model, n and

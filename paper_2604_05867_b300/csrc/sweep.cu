@@ -1079,6 +1079,38 @@ __device__ __forceinline__ void gather_row_L(T *buf, const T *__restrict__ Lz, c
     }
 }
 
+// The same gather as one flat pass (CH * NT * 4 = 2^(n2+1) codes): chunk k
+// holds codes 4k .. 4k+3, whose length l and source run follow from the code
+// itself, so every thread issues all of its loads before its first store.
+template <typename T, int NT, int CH>
+__device__ __forceinline__ void gather_row_L_flat(T *buf, const T *__restrict__ Lz, const T *__restrict__ om,
+                                                  uint32_t c1, int j) {
+    T a4[CH][4];
+    T wl[CH];
+#pragma unroll
+    for (int i = 0; i < CH; i++) {
+        const uint32_t code = 4u * (threadIdx.x + i * NT);
+        if (code >= 4) {
+            const int l = 31 - __clz(code);
+            wl[i] = om[j + l];
+            ld4(Lz + ((size_t)c1 << l) + (code - (1u << l)), a4[i]);
+        } else {
+            // codes 1, 2, 3: c1.0 ... (l = 0: the code c1 itself; l = 1: c1 0, c1 1)
+            wl[i] = (T)1;
+            a4[i][0] = (T)0;
+            a4[i][1] = om[j] * Lz[c1];
+            a4[i][2] = om[j + 1] * Lz[(size_t)c1 << 1];
+            a4[i][3] = om[j + 1] * Lz[((size_t)c1 << 1) | 1u];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < CH; i++) {
+#pragma unroll
+        for (int k = 0; k < 4; k++) a4[i][k] = wl[i] * a4[i][k];
+        st4(buf + 4u * (threadIdx.x + i * NT), a4[i]);
+    }
+}
+
 // pass 2 adjoint (rows): gather omega_k L(code c1 . c2) over the row, adjoint
 // sweep over x2, write the row's top half to Gb[c1][x2].
 template <typename T, int R, bool HALF>
@@ -1535,7 +1567,8 @@ __global__ void __launch_bounds__(1 << LT) k_rows_adj_l(SweepArgs a, const T *Ls
     const int n2 = a.n2, n = a.n;  // n2 = NL + LT
     const uint32_t c1 = HALF ? half_row(blockIdx.x) : blockIdx.x + 1;
     const int j = bitlen32(c1) - 1;
-    gather_row_L<T, ROW_THREADS>(buf, Lsrc + z * a.strideM, omega + z * (n + 1), c1, j, n2);
+    // (2^(n2+1) codes = NI / 2 chunks of 4 per thread)
+    gather_row_L_flat<T, ROW_THREADS, NI / 2>(buf, Lsrc + z * a.strideM, omega + z * (n + 1), c1, j);
     __syncthreads();
     lsweep_adj_any<T, 2 * NI, ROW_THREADS>(buf, n2, 0, NL);
     const uint32_t sigma = threadIdx.x;
