@@ -967,7 +967,9 @@ __global__ void __launch_bounds__(256) k_combine_k(SweepArgs a, const T *__restr
                                                    T *__restrict__ q, T *__restrict__ L, int mode) {
     constexpr int KB = CMB_LOG + (HALF ? 1 : 0);
     const int z = blockIdx.y;
-    if (!flag_set(a.inst + z * INST_STRIDE, I_ACTIVE)) return;
+    // the instance flag is tested only once the first global loads are in
+    // flight (the loads before the test read valid memory of any instance)
+    const bool active = flag_set(a.inst + z * INST_STRIDE, I_ACTIVE);
     const int n1 = a.n1, n2 = a.n2, n = a.n;
     const T *pz = p + z * a.strideN, *Fz = F1 + z * a.strideN, *Tmz = Tm + z * a.strideM;
     const T *Tsz = Ts + z * ((size_t)32 << (n1 + 1));
@@ -1031,6 +1033,7 @@ __global__ void __launch_bounds__(256) k_combine_k(SweepArgs a, const T *__restr
                 acc[r] += v;
             }
         }
+        if (!active) return;
 #pragma unroll
         for (int r = 0; r < RC; r++) {
             const uint32_t y = y0 + r * 256 + threadIdx.x;
@@ -1389,29 +1392,37 @@ k_cols_adj_l(SweepArgs a, EpiArgs ep, const T *__restrict__ Gb, T *__restrict__ 
     __shared__ T red2[2 * CT / 32];
     constexpr int NI = 1 << NL;
     const int z = blockIdx.y;
-    if (!flag_set(a.inst + z * INST_STRIDE, I_ACTIVE)) return;
+    // the instance flag is tested only once the first global loads are in
+    // flight (the loads before the test read valid memory of any instance)
+    const bool active = flag_set(a.inst + z * INST_STRIDE, I_ACTIVE);
+    const T shift = STEP ? (T)a.inst[z * INST_STRIDE + I_SHIFT] : (T)0;
     const int n1 = a.n1, n2 = a.n2, lw = a.lw, L = n1 - NL;
     const uint32_t w = 1u << lw, col0 = blockIdx.x << lw;
     const uint32_t nall = (2u << n1) << lw;
     const T *Gz = Gb + z * a.strideM;
     const uint32_t full2 = (1u << n2) - 1u;
     if (lw >= 2) {
-#pragma unroll 4
-        for (uint32_t e = 4 * threadIdx.x; e < nall; e += 4 * CT) {
-            uint32_t row = e >> lw, cc = e & (w - 1u);
-            T t4[4] = {(T)0, (T)0, (T)0, (T)0};
+        // the tile holds 2^(NL+1) CT elements: NI / 2 chunks of 4 per thread,
+        // all loaded before the first store
+        T t4[NI / 2][4];
+#pragma unroll
+        for (int i = 0; i < NI / 2; i++) {
+            const uint32_t e = 4u * (threadIdx.x + i * CT), row = e >> lw, cc = e & (w - 1u);
+#pragma unroll
+            for (int k = 0; k < 4; k++) t4[i][k] = (T)0;
             if (row) {
                 if (!HALF || in_h1(row)) {
-                    ld4(Gz + (((size_t)row << n2) | (col0 + cc)), t4);
+                    ld4(Gz + (((size_t)row << n2) | (col0 + cc)), t4[i]);
                 } else {
                     // rows outside H1: complement row, complement columns (reversed)
                     T t[4];
                     ld4(Gz + (((size_t)cpl_code(row) << n2) | (full2 - (col0 + cc) - 3u)), t);
-                    t4[0] = t[3]; t4[1] = t[2]; t4[2] = t[1]; t4[3] = t[0];
+                    t4[i][0] = t[3]; t4[i][1] = t[2]; t4[i][2] = t[1]; t4[i][3] = t[0];
                 }
             }
-            st4(buf + e, t4);
         }
+#pragma unroll
+        for (int i = 0; i < NI / 2; i++) st4(buf + 4u * (threadIdx.x + i * CT), t4[i]);
     } else {
         for (uint32_t e = threadIdx.x; e < nall; e += CT) {
             uint32_t row = e >> lw, cc = e & (w - 1u);
@@ -1421,6 +1432,7 @@ k_cols_adj_l(SweepArgs a, EpiArgs ep, const T *__restrict__ Gb, T *__restrict__ 
             buf[e] = t;
         }
     }
+    if (!active) return;
     __syncthreads();
     lsweep_adj_any<T, 2 * NI, CT>(buf, n1, lw, NL);
     const uint32_t c = threadIdx.x & (w - 1u), sigma = threadIdx.x >> lw;
@@ -1466,7 +1478,6 @@ k_cols_adj_l(SweepArgs a, EpiArgs ep, const T *__restrict__ Gb, T *__restrict__ 
         T tP = (T)0;
 #pragma unroll
         for (int r = 0; r < NI; r++) tP += v[NI + r];
-        const T shift = (T)a.inst[z * INST_STRIDE + I_SHIFT];
 #pragma unroll
         for (int r = 0; r < NI; r++) v[NI + r] = v[NI + r] * exp2_t<T>(v[r] - shift);
 #pragma unroll
@@ -1516,7 +1527,9 @@ k_rows_fwd_l(SweepArgs a, const T *p, const T *F1, T *Tm, T *Ts) {
     T *buf = reinterpret_cast<T *>(smem_raw);
     constexpr int NI = 1 << NL;
     const int z = blockIdx.y;
-    if (!flag_set(a.inst + z * INST_STRIDE, I_ACTIVE)) return;
+    // the instance flag is tested only once the first global loads are in
+    // flight (the loads before the test read valid memory of any instance)
+    const bool active = flag_set(a.inst + z * INST_STRIDE, I_ACTIVE);
     const int n1 = a.n1, n2 = a.n2;  // n2 = NL + LT
     const uint32_t c1 = HALF ? half_row(blockIdx.x) : blockIdx.x + 1;
     const uint32_t half = 1u << n2, sigma = threadIdx.x;
@@ -1535,6 +1548,7 @@ k_rows_fwd_l(SweepArgs a, const T *p, const T *F1, T *Tm, T *Ts) {
         const uint32_t x2 = ((uint32_t)r << LT) | sigma;  // (L == LT)
         v[NI + r] = (HALF && x2 >= (half >> 1)) ? srcm[half - 1u - x2] : src[x2];
     }
+    if (!active) return;
     local_fwd<T, NL>(v);
 #pragma unroll
     for (int r = 1; r < 2 * NI; r++) buf[(r << LT) | sigma] = v[r];  // (L == LT)
@@ -1563,12 +1577,15 @@ __global__ void __launch_bounds__(1 << LT) k_rows_adj_l(SweepArgs a, const T *Ls
     T *buf = reinterpret_cast<T *>(smem_raw);
     constexpr int NI = 1 << NL;
     const int z = blockIdx.y;
-    if (!flag_set(a.inst + z * INST_STRIDE, I_ACTIVE)) return;
+    // the instance flag is tested only once the first global loads are in
+    // flight (the loads before the test read valid memory of any instance)
+    const bool active = flag_set(a.inst + z * INST_STRIDE, I_ACTIVE);
     const int n2 = a.n2, n = a.n;  // n2 = NL + LT
     const uint32_t c1 = HALF ? half_row(blockIdx.x) : blockIdx.x + 1;
     const int j = bitlen32(c1) - 1;
     // (2^(n2+1) codes = NI / 2 chunks of 4 per thread)
     gather_row_L_flat<T, ROW_THREADS, NI / 2>(buf, Lsrc + z * a.strideM, omega + z * (n + 1), c1, j);
+    if (!active) return;
     __syncthreads();
     lsweep_adj_any<T, 2 * NI, ROW_THREADS>(buf, n2, 0, NL);
     const uint32_t sigma = threadIdx.x;
