@@ -1445,16 +1445,21 @@ k_cols_adj_l(SweepArgs a, EpiArgs ep, const T *__restrict__ Gb, T *__restrict__ 
     // (STEP reads and rewrites p through this one pointer)
     T *__restrict__ pz = (STEP ? pw : const_cast<T *>(reinterpret_cast<const T *>(ep.p))) + z * a.strideN;
     T *__restrict__ Dz = STEP ? nullptr : reinterpret_cast<T *>(ep.Dout) + z * a.strideN;
-    // all of a thread's global loads are issued before its first store, in two
-    // rounds that fit the registers: Hb into the rows below 2^NL of v (dead
-    // after the local steps), D = -Hb - G there, then p over the G rows
+    // all of a thread's global loads are issued at once, before its first
+    // store: Hb into the rows below 2^NL of v (dead after the local steps),
+    // p beside it; then D = -Hb - G, and p takes the G rows
     const size_t x0 = ((size_t)sigma << n2) | (col0 + c), xs = (size_t)1 << (L + n2);
+    T pv[NI];
 #pragma unroll
-    for (int r = 0; r < NI; r++) v[r] = Hbz[x0 + r * xs];
+    for (int r = 0; r < NI; r++) {
+        v[r] = Hbz[x0 + r * xs];
+        pv[r] = pz[x0 + r * xs];
+    }
 #pragma unroll
-    for (int r = 0; r < NI; r++) v[r] = -v[r] - v[NI + r];
-#pragma unroll
-    for (int r = 0; r < NI; r++) v[NI + r] = pz[x0 + r * xs];
+    for (int r = 0; r < NI; r++) {
+        v[r] = -v[r] - v[NI + r];
+        v[NI + r] = pv[r];
+    }
     T tZ = (T)0, tM = (T)-INFINITY;
 #pragma unroll
     for (int r = 0; r < NI; r++) {
