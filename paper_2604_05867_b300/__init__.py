@@ -42,7 +42,8 @@ class Options(ctypes.Structure):
                 ("sched_n2_fp32", ctypes.c_int), ("sched_w_fp32", ctypes.c_int),
                 ("sched_n2_fp64", ctypes.c_int), ("sched_w_fp64", ctypes.c_int),
                 ("enable_literal", ctypes.c_int), ("use_half", ctypes.c_int),
-                ("use_regsteps", ctypes.c_int), ("fuse_update", ctypes.c_int)]
+                ("use_regsteps", ctypes.c_int), ("fuse_update", ctypes.c_int),
+                ("use_tma", ctypes.c_int)]
 
 
 _lib = None

@@ -240,6 +240,7 @@ extern "C" void bdc_default_options(bdc_options *o) {
     o->use_half = 1;
     o->use_regsteps = 15;
     o->fuse_update = 1;
+    o->use_tma = 0;
 }
 
 extern "C" bdc_status bdc_create(int n, const double *d, int nd, const bdc_options *opt, bdc_engine **out) {

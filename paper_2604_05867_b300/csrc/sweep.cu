@@ -25,7 +25,10 @@
 // per iteration instead of once per symbol.
 #include "bdc_internal.cuh"
 
+#include <cuda.h>
+
 #include <algorithm>
+#include <cstring>
 #include <type_traits>
 
 namespace {
@@ -682,6 +685,46 @@ __device__ __forceinline__ bool in_h1(uint32_t c) {
     return j == 0 || !((c >> (j - 1)) & 1u);
 }
 
+// ---------------------------------------------------------------------------
+// TMA (cp.async.bulk.tensor) and mbarrier, inline PTX (sm_90 and later)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *ptr) {
+    return (uint32_t)__cvta_generic_to_shared(ptr);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *m, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *m, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(m)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *m, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(m)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// one 2-D box (x = innermost coordinate, in elements) into shared memory;
+// completion is counted in bytes on the mbarrier
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tm, int x, int y, uint64_t *m) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(smem_u32(m))
+        : "memory");
+}
+// bounded wait for phase `parity` (about a second at most); false: gave up
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *m, uint32_t parity) {
+    for (uint32_t it = 0; it < (1u << 22); it++)
+        if (mbar_try_wait(m, parity)) return true;
+    return false;
+}
+
 struct SweepArgs {
     int n, n1, n2, lw;
     int nblk;                 // column CTAs per instance
@@ -694,7 +737,20 @@ struct SweepArgs {
     // FP32 copies of the two constants, so FP32 kernels convert nothing
     float q_floor_f;
     float inv_binom_f[BDC_MAXN + 2];
+    // column step kernel: load the Gb tile with TMA through the kernel's
+    // tensor map (complement half mode, 4 columns, n1 >= 9; see k_cols_adj_l)
+    int tma;
 };
+
+// rows of the Gb tile that the TMA form loads, in 256-row boxes: slots 0, 1
+// are rows [0, 512); for lengths m >= 9, slots 2^(m-9) + 1 + i are the H1
+// rows 2^m + 256 i (i < 2^(m-9)).  nslot = 2^(n1-8) + 1.
+__device__ __forceinline__ uint32_t tma_slot_row(uint32_t s) {
+    if (s < 2u) return 256u * s;
+    const uint32_t t = s - 1u;  // in [2^(m-9), 2^(m-8))
+    const int m = 9 + (31 - __clz(t));
+    return (1u << m) + 256u * (t - (1u << (m - 9)));
+}
 
 template <typename T>
 __device__ __forceinline__ T inv_binom_t(const SweepArgs &a, int k);
@@ -1385,9 +1441,12 @@ k_cols_fwd_l(SweepArgs a, T *__restrict__ p, const T *__restrict__ D, T *__restr
 template <typename T, int NL, bool HALF, bool STEP, int CT>
 __global__ void __launch_bounds__(CT, CT >= 1024 ? 1 : tile_blocks<T>((size_t)CT * (2 << NL) * sizeof(T), 2))
 k_cols_adj_l(SweepArgs a, EpiArgs ep, const T *__restrict__ Gb, T *__restrict__ pw, T *__restrict__ F1,
-             int keep_p = 1) {  // keep_p = 0: the updated p is not stored (schedule timing)
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *buf = reinterpret_cast<T *>(smem_raw);
+             int keep_p,  // 0: the updated p is not stored (schedule timing)
+             const __grid_constant__ CUtensorMap tmG) {  // Gb as [nd 2^(n1+1) rows][2^n2], used when a.tma
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // the TMA form needs a 128-byte aligned tile (its launch adds 128 bytes of
+    // dynamic shared memory for this); the dynamic area follows the static one
+    T *buf = reinterpret_cast<T *>(smem_raw + (a.tma ? ((0u - smem_u32(smem_raw)) & 127u) : 0u));
     __shared__ T red[2 * CT / 32];
     __shared__ T red2[2 * CT / 32];
     constexpr int NI = 1 << NL;
@@ -1401,7 +1460,67 @@ k_cols_adj_l(SweepArgs a, EpiArgs ep, const T *__restrict__ Gb, T *__restrict__ 
     const uint32_t nall = (2u << n1) << lw;
     const T *Gz = Gb + z * a.strideM;
     const uint32_t full2 = (1u << n2) - 1u;
-    if (lw >= 2) {
+    bool tma_done = false;
+    if constexpr (HALF && STEP && sizeof(T) == 4) {
+        // (alignment of the boxes' shared-memory destinations and of the tensor
+        // map; anything else keeps the per-thread loads below)
+        if (a.tma && (smem_u32(buf) & 127u) == 0 && (reinterpret_cast<uintptr_t>(&tmG) & 63u) == 0) {
+            // TMA form (4 columns, n1 >= 9): the H1 rows at this CTA's columns
+            // straight into the tile, and at the mirror columns
+            // 2^n2 - col0 - 4 .. 2^n2 - col0 - 1 into a staging area after it;
+            // each row outside H1 is then its complement row of the staging
+            // area with the 4 columns reversed (rows [0, 512) are loaded whole
+            // and their rows outside H1 overwritten the same way)
+            __shared__ __align__(8) uint64_t mbar;
+            T *stage = buf + nall;
+            const uint32_t nslot = (1u << (n1 - 8)) + 1u;
+            if (threadIdx.x == 0) {
+                mbar_init(&mbar, 1);
+                mbar_fence_init();
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                mbar_expect_tx(&mbar, 2u * nslot * 256u * 4u * (uint32_t)sizeof(T));
+                const int y0 = z << (n1 + 1), xm = (int)(full2 - col0 - 3u);
+                for (uint32_t sl = 0; sl < nslot; sl++) {
+                    const uint32_t row0 = tma_slot_row(sl);
+                    tma_load_2d(buf + (row0 << 2), &tmG, (int)col0, y0 + (int)row0, &mbar);
+                    tma_load_2d(stage + ((sl * 256u) << 2), &tmG, xm, y0 + (int)row0, &mbar);
+                }
+            }
+            const bool ok = mbar_wait_bounded(&mbar, 0);
+            if (__syncthreads_or(!ok)) {
+                // a copy did not arrive in time: report, wait (bounded) for the
+                // copies still in flight into this CTA's shared memory, return
+                if (threadIdx.x == 0) {
+                    const_cast<double *>(a.inst)[z * INST_STRIDE + I_STATUS] = (double)BDC_ETIMEOUT;
+                    (void)mbar_wait_bounded(&mbar, 0);
+                }
+                __syncthreads();
+                return;
+            }
+            if (!active) return;
+            // rows outside H1 (row 0 is zero): k in [2^(j-1), 2^j) is row
+            // 2^j | k of length j, complement row 2^j | (2^j - 1 - k)
+            for (uint32_t k = threadIdx.x; k < (1u << n1); k += CT) {
+                T t4[4] = {(T)0, (T)0, (T)0, (T)0};
+                uint32_t r = 0;
+                if (k > 0) {
+                    const int j = bitlen32(k);
+                    r = (1u << j) | k;
+                    const uint32_t qo = ((1u << j) - 1u) ^ k, q = (1u << j) | qo;
+                    const uint32_t srow = (q < 512u) ? q : (((1u << (j - 9)) + 1u) << 8) + qo;
+                    T t[4];
+                    ld4(stage + (srow << 2), t);
+                    t4[0] = t[3]; t4[1] = t[2]; t4[2] = t[1]; t4[3] = t[0];
+                }
+                st4(buf + (r << 2), t4);
+            }
+            tma_done = true;
+        }
+    }
+    if (tma_done) {
+    } else if (lw >= 2) {
         // the tile holds 2^(NL+1) CT elements: NI / 2 chunks of 4 per thread,
         // all loaded before the first store
         T t4[NI / 2][4];
@@ -1603,6 +1722,44 @@ __global__ void __launch_bounds__(1 << LT) k_rows_adj_l(SweepArgs a, const T *Ls
 #pragma unroll
     for (int r = 0; r < NI; r++) Gz[(r << LT) | sigma] = v[NI + r];
 }
+
+// cuTensorMapEncodeTiled from the driver (the library links the runtime only)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(ptr);
+        else
+            (void)cudaGetLastError();
+    }
+    return fn;
+}
+
+// tensor map of an FP32 [nd][2^(n1+1)][2^n2] array seen as rows of 2^n2, box
+// 4 columns x 256 rows; false where TMA does not apply or encoding fails
+static bool tma_map_rows4(const float *base, int nd, int n1, int n2, CUtensorMap *out) {
+    EncodeTiledFn fn = encode_tiled_fn();
+    if (!fn || (reinterpret_cast<uintptr_t>(base) & 15u) != 0) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)1 << n2, (cuuint64_t)nd << (n1 + 1)};
+    cuuint64_t strides[1] = {((cuuint64_t)1 << n2) * sizeof(float)};
+    cuuint32_t box[2] = {4, 256};
+    cuuint32_t es[2] = {1, 1};
+    return fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// bytes of the TMA form's staging area (the mirror columns' H1 row boxes)
+static size_t tma_stage_bytes(int n1) { return (((size_t)1 << (n1 - 8)) + 1) * 256 * 4 * sizeof(float); }
 
 template <typename T>
 SweepArgs make_args(bdc_engine *e, PrecBuf<T> &b) {
@@ -1905,18 +2062,26 @@ bdc_status sweep_adjoint(bdc_engine *e, PrecBuf<T> &b, const T *Lsrc, const T *o
     const int rc = r_of(((size_t)2 << s.n1) << s.lw);
     const int nlc = (mode == MODE_ITER) ? nl_cols<T>(e, s, 8) : 0;
     const int ct = ct_cols<T>(s);
+    CUtensorMap tmG;
+    memset(&tmG, 0, sizeof(tmG));
+    a.tma = 0;
+    if (sizeof(T) == 4 && step && nlc && half && e->opt.use_tma && s.lw == 2 && s.n1 >= 9 && ct == 512 &&
+        tma_map_rows4(reinterpret_cast<const float *>(b.Gb), e->nd, s.n1, s.n2, &tmG)) {
+        a.tma = 1;
+        sm1 += tma_stage_bytes(s.n1) + 128;
+    }
     if (step && nlc && half)
         SW_WITH_CT(ct, SW_WITH_NL(T, nlc, (k_cols_adj_l<T, NL, true, true, CT><<<g1, CT, sm1, e->stream>>>(
-                                              a, ep, b.Gb, b.p, b.F1, keep_p ? 1 : 0))));
+                                              a, ep, b.Gb, b.p, b.F1, keep_p ? 1 : 0, tmG))));
     else if (step && nlc)
         SW_WITH_CT(ct, SW_WITH_NL(T, nlc, (k_cols_adj_l<T, NL, false, true, CT><<<g1, CT, sm1, e->stream>>>(
-                                              a, ep, b.Gb, b.p, b.F1, keep_p ? 1 : 0))));
+                                              a, ep, b.Gb, b.p, b.F1, keep_p ? 1 : 0, tmG))));
     else if (nlc && half)
         SW_WITH_CT(ct, SW_WITH_NL(T, nlc, (k_cols_adj_l<T, NL, true, false, CT><<<g1, CT, sm1, e->stream>>>(
-                                              a, ep, b.Gb, nullptr, nullptr))));
+                                              a, ep, b.Gb, nullptr, nullptr, 1, tmG))));
     else if (nlc)
         SW_WITH_CT(ct, SW_WITH_NL(T, nlc, (k_cols_adj_l<T, NL, false, false, CT><<<g1, CT, sm1, e->stream>>>(
-                                              a, ep, b.Gb, nullptr, nullptr))));
+                                              a, ep, b.Gb, nullptr, nullptr, 1, tmG))));
     else if (half)
         SW_WITH_R(rmax_adj<T>(), rc,
                   (k_cols_adj<T, R, true><<<g1, SW_THREADS, sm1, e->stream>>>(a, ep, b.Gb, Lsrc, omega, mode)));

@@ -408,3 +408,51 @@ def test_stepped_instances_stop_independently():
     for e in ref:
         e.close()
     both.close()
+
+
+@pytest.mark.parametrize("n,n2,ds", [(18, 8, [0.3, 0.7]), (19, 10, [0.5])])
+def test_tma_tile_load_is_bit_identical(n, n2, ds):
+    # the one-pass iteration boundary with its Gb tile loaded by TMA (FP32,
+    # complement half mode, 4 columns, n1 = n - n2 >= 9; two instances: the
+    # tensor map spans both) against the same kernels with per-thread loads:
+    # the same values reach the same arithmetic, so bounds and p agree bit for bit
+    import paper_2604_05867_b300 as bdc
+    T = 6
+    kw = dict(sched_n2_fp32=n2, sched_w_fp32=4, enable_literal=0, chunk=3)
+    a = bdc.Engine(n, ds, options=bdc.default_options(use_tma=1, **kw))
+    b = bdc.Engine(n, ds, options=bdc.default_options(use_tma=0, **kw))
+    assert a.schedule("fp32") == {"n1": n - n2, "n2": n2, "width": 4}
+    a.iterate(T, -1.0, "fp32", "sweep")
+    b.iterate(T, -1.0, "fp32", "sweep")
+    for z in range(len(ds)):
+        la, ua = a.history(z)
+        lb, ub = b.history(z)
+        assert len(la) == T and np.array_equal(la, lb) and np.array_equal(ua, ub)
+    assert np.array_equal(a.get_p(), b.get_p())
+    a.close()
+    b.close()
+
+
+def test_tma_bench_configuration_matches_oracle_bounds():
+    # n = 24 in the headline bench's configuration (split 11 + 13, 4 columns,
+    # FP32, stepped, TMA tile loads): bit-identical to per-thread loads, and
+    # within FP32 rounding of the FP64 sweep's bounds (the FP64 sweep at this
+    # size is checked against the oracle in test_full_size_bench_configuration)
+    import paper_2604_05867_b300 as bdc
+    n, d, T = 24, 0.5, 3
+    kw = dict(sched_n2_fp32=13, sched_w_fp32=4, sched_n2_fp64=13, sched_w_fp64=4, enable_literal=0)
+    a = bdc.Engine(n, [d], options=bdc.default_options(use_tma=1, **kw))
+    b = bdc.Engine(n, [d], options=bdc.default_options(use_tma=0, **kw))
+    a.iterate(T, -1.0, "fp32", "sweep")
+    b.iterate(T, -1.0, "fp32", "sweep")
+    la, ua = a.history(0)
+    lb, ub = b.history(0)
+    assert np.array_equal(la, lb) and np.array_equal(ua, ub)
+    assert np.array_equal(a.get_p(), b.get_p())
+    b.close()
+    c = bdc.Engine(n, [d], options=bdc.default_options(**kw))
+    c.iterate(T, -1.0, "fp64", "sweep")
+    lc, uc = c.history(0)
+    assert np.all(np.abs(la - lc) <= 2e-5 * np.abs(lc)) and np.all(np.abs(ua - uc) <= 2e-5 * np.abs(uc))
+    a.close()
+    c.close()
