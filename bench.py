@@ -75,6 +75,21 @@ def stage_bytes(n: int, n1: int, n2: int, elem: int, half: bool) -> dict:
 # (profiles/<kernel>_n24.md), keyed by stage, n and the (n1, n2, width)
 # schedule.  A kernel changed since its capture must be removed from here.
 MEASURED_TRAFFIC = {
+    ("cols_step", 24, 11, 13, 4): 134.635008e6 + 30.761472e6,
+    ("cols_step", 24, 11, 13, 8): 134.29888e6 + 36.823808e6,
+    ("rows_adj", 24, 11, 13, 4): 75.447552e6 + 34.15168e6,
+    ("combine", 24, 11, 13, 4): 134.219008e6 + 27.436544e6,
+    ("rows_fwd", 24, 11, 13, 4): 67.13984e6 + 20.333312e6,
+}
+
+# Shared-memory wavefronts (128 B each) per launch of the same kernels, from
+# the same captures (l1tex__data_pipe_lsu_wavefronts_mem_shared.sum): the
+# shared-memory sweep kernels are bound by shared memory, not by DRAM.
+MEASURED_SMEM_WAVEFRONTS = {
+    ("cols_step", 24, 11, 13, 4): 14724270,
+    ("cols_step", 24, 11, 13, 8): 14905774,
+    ("rows_adj", 24, 11, 13, 4): 18092612,
+    ("rows_fwd", 24, 11, 13, 4): 14390558,
 }
 
 
@@ -280,6 +295,17 @@ def run_ours(args, rank: int, world: int):
                     "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                     "peak_source": peaks["source"], "algorithmic_bytes": sb[top],
                     "note": "complement half mode: %s" % half}
+            wf = MEASURED_SMEM_WAVEFRONTS.get((top, n, sched32["n1"], sched32["n2"], sched32["width"]))
+            if wf is not None:
+                # the kernel's binding resource: shared-memory bandwidth, 128 B
+                # per SM per clock at the maximum SM clock
+                props = torch.cuda.get_device_properties(dev)
+                smem_peak = props.multi_processor_count * 128 * (clk.get("sm_max_mhz") or 2032.0) * 1e6 / 1e12
+                smem_tb = wf * 128 / (stages[top] / 1000.0) / 1e12
+                roof["shared_memory"] = {"bytes_per_launch": wf * 128, "achieved": smem_tb, "peak": smem_peak,
+                                         "unit": "TB/s", "frac": smem_tb / smem_peak,
+                                         "source": "ncu shared-memory wavefronts of one launch x 128 B / "
+                                                   "this run's event time; peak = SMs x 128 B/clk x max SM clock"}
             stage_total = sum(stages.values())
 
             # FP64 sweep iteration (same-algorithm precision baseline)
