@@ -1052,9 +1052,12 @@ __global__ void __launch_bounds__(256) k_combine_k(SweepArgs a, const T *__restr
         T acc[RC];
 #pragma unroll
         for (int r = 0; r < RC; r++) acc[r] = (T)0;
+#pragma unroll 2
         for (int j = jlo; j <= jhi; j++) {
             const int l = k - j;
-            if (!small && l >= CMB_LOG) {
+            // (a second part of exactly CMB_LOG = n2 symbols spans both of its
+            // halves within one CTA, so their complement choice is per code)
+            if (!small && l >= CMB_LOG && !(HALF && l == n2 && l == CMB_LOG)) {
                 // the CTA's codes share y >> l (y0 is a multiple of 2^CMB_LOG):
                 // the term of code y0 + t is src[+-t] for one base per CTA
                 const uint32_t u20 = y0 & ((1u << l) - 1u);

@@ -456,3 +456,25 @@ def test_tma_bench_configuration_matches_oracle_bounds():
     assert np.all(np.abs(la - lc) <= 2e-5 * np.abs(lc)) and np.all(np.abs(ua - uc) <= 2e-5 * np.abs(uc))
     a.close()
     c.close()
+
+
+@pytest.mark.parametrize("n2", [9, 10, 11])
+def test_combine_split_boundaries_fp32(n2):
+    # the combine's split of an output code into u1 u2 at every length of the
+    # second part around the CTA width (1024 codes): FP32 stepped half-mode
+    # iterations at n = 19 against the all-shared-memory, unstepped, full-mode
+    # FP64 kernels (a mistake at one split length moves the bounds far beyond
+    # FP32 rounding)
+    import paper_2604_05867_b300 as bdc
+    n, d, T = 19, 0.6, 3
+    a = bdc.Engine(n, [d], options=bdc.default_options(sched_n2_fp32=n2, sched_w_fp32=4, enable_literal=0))
+    assert a.schedule("fp32")["n2"] == n2
+    a.iterate(T, -1.0, "fp32", "sweep")
+    b = bdc.Engine(n, [d], options=bdc.default_options(sched_n2_fp64=n2, sched_w_fp64=4, enable_literal=0,
+                                                       use_regsteps=0, fuse_update=0, use_half=0))
+    b.iterate(T, -1.0, "fp64", "sweep")
+    la, ua = a.history(0)
+    lb, ub = b.history(0)
+    assert np.all(np.abs(la - lb) <= 2e-5 * np.abs(lb)) and np.all(np.abs(ua - ub) <= 2e-5 * np.abs(ub))
+    a.close()
+    b.close()
