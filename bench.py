@@ -78,6 +78,7 @@ MEASURED_TRAFFIC = {
     ("cols_step", 24, 11, 13, 4): 134.635008e6 + 30.761472e6,
     ("cols_step", 24, 11, 13, 8): 134.29888e6 + 36.823808e6,
     ("rows_adj", 24, 11, 13, 4): 75.447552e6 + 34.15168e6,
+    ("combine", 24, 11, 13, 4): 134.210304e6 + 28.534528e6,
     ("rows_fwd", 24, 11, 13, 4): 67.13984e6 + 20.333312e6,
 }
 
