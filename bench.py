@@ -358,6 +358,11 @@ def run_ours(args, rank: int, world: int):
             # end to end through the public API: one Engine.iterate(1) call per
             # step, bounds read back to the host every step
             K = max(10, min(args.steps, 50))
+            # (setup, as for the timed region above: the replayed graphs are built
+            # and three untimed calls run first)
+            eng.prepare("fp32", "sweep")
+            for _ in range(3):
+                eng.iterate(1, -1.0, "fp32", "sweep")
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             for _ in range(K):

@@ -140,8 +140,10 @@ struct bdc_engine {
     PrecBuf<float> f32;
     PrecBuf<double> f64;
 
-    // graph cache per (precision, impl)
+    // graph cache per (precision, impl): `chunk` iterations, and one iteration
+    // (calls that ask for fewer than `chunk`)
     cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    cudaGraphExec_t graph1[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     int cur = 0;                // representation holding the current p: 0 FP32, 1 FP64, 2 literal
     bool half_ok = true;        // p is complement-invariant (uniform start, BA iterates)
     bool orbit_ok = true;       // p is invariant under complement and reversal
@@ -152,6 +154,7 @@ struct bdc_engine {
     int64_t iters_total = 0;
     int64_t launches = 0;       // kernels launched so far (graph replays included)
     int64_t graph_kernels[2][2] = {{0, 0}, {0, 0}};
+    int64_t graph1_kernels[2][2] = {{0, 0}, {0, 0}};
     // stage profiling: when prof_n >= 0, each stage boundary records an event
     cudaEvent_t prof_ev[32];
     const char *prof_name[32];

@@ -272,8 +272,10 @@ extern "C" size_t bdc_workspace_bytes(const bdc_engine *e) { return e ? e->ws_by
 extern "C" void bdc_destroy(bdc_engine *e) {
     if (!e) return;
     for (int a = 0; a < 2; a++)
-        for (int b = 0; b < 2; b++)
+        for (int b = 0; b < 2; b++) {
             if (e->graph[a][b]) cudaGraphExecDestroy(e->graph[a][b]);
+            if (e->graph1[a][b]) cudaGraphExecDestroy(e->graph1[a][b]);
+        }
     if (e->prof_created)
         for (int i = 0; i < 32; i++) cudaEventDestroy(e->prof_ev[i]);
     delete e;
@@ -441,13 +443,22 @@ static bdc_status unhalf(bdc_engine *e) {
     return BDC_OK;
 }
 
+// drop the cached graphs of one precision (both impls, both lengths)
+static void drop_graphs_prec(bdc_engine *e, int prec) {
+    for (int b = 0; b < 2; b++) {
+        if (e->graph[prec][b]) {
+            cudaGraphExecDestroy(e->graph[prec][b]);
+            e->graph[prec][b] = nullptr;
+        }
+        if (e->graph1[prec][b]) {
+            cudaGraphExecDestroy(e->graph1[prec][b]);
+            e->graph1[prec][b] = nullptr;
+        }
+    }
+}
+
 static void drop_graphs(bdc_engine *e) {
-    for (int a = 0; a < 2; a++)
-        for (int b = 0; b < 2; b++)
-            if (e->graph[a][b]) {
-                cudaGraphExecDestroy(e->graph[a][b]);
-                e->graph[a][b] = nullptr;
-            }
+    for (int a = 0; a < 2; a++) drop_graphs_prec(e, a);
 }
 
 static bdc_status materialize(bdc_engine *e) {
@@ -575,8 +586,9 @@ static bdc_status iter_once(bdc_engine *e, int prec, int impl) {
     return prec == BDC_FP32 ? iter_sweep<float>(e, e->f32, 0) : iter_sweep<double>(e, e->f64, 1);
 }
 
-static bdc_status get_graph(bdc_engine *e, int prec, int impl, cudaGraphExec_t *out) {
-    cudaGraphExec_t &g = e->graph[prec][impl];
+// the cached graph of `chunk` iterations (one == false) or of one iteration
+static bdc_status get_graph(bdc_engine *e, int prec, int impl, cudaGraphExec_t *out, bool one = false) {
+    cudaGraphExec_t &g = one ? e->graph1[prec][impl] : e->graph[prec][impl];
     // a graph of stepped iterations starts from a current F1 (eager, not captured)
     if (impl == BDC_SWEEP) BDC_TRY(ensure_primed(e, prec));
     if (!g) {
@@ -584,9 +596,10 @@ static bdc_status get_graph(bdc_engine *e, int prec, int impl, cudaGraphExec_t *
         const int64_t before = e->launches;
         BDC_CUDA_TRY(cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal));
         bdc_status st = BDC_OK;
-        for (int i = 0; i < e->opt.chunk && st == BDC_OK; i++) st = iter_once(e, prec, impl);
+        const int iters = one ? 1 : e->opt.chunk;
+        for (int i = 0; i < iters && st == BDC_OK; i++) st = iter_once(e, prec, impl);
         cudaError_t ce = cudaStreamEndCapture(e->stream, &graph);
-        e->graph_kernels[prec][impl] = e->launches - before;  // recorded, not yet run
+        (one ? e->graph1_kernels : e->graph_kernels)[prec][impl] = e->launches - before;  // recorded, not yet run
         e->launches = before;
         if (st != BDC_OK) return st;
         if (ce != cudaSuccess) BDC_FAIL(BDC_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
@@ -613,6 +626,7 @@ extern "C" bdc_status bdc_prepare(bdc_engine *e, int prec, int impl) {
     if (e->opt.use_graph && e->stream != nullptr) {
         cudaGraphExec_t g;
         BDC_TRY(get_graph(e, prec, impl, &g));
+        if (e->opt.chunk > 1) BDC_TRY(get_graph(e, prec, impl, &g, true));
     }
     return sync_check(e, "bdc_prepare");
 }
@@ -639,6 +653,14 @@ extern "C" bdc_status bdc_ba_iterate(bdc_engine *e, int max_iters, double tol, i
             BDC_TRY(get_graph(e, prec, impl, &g));
             BDC_CUDA_TRY(cudaGraphLaunch(g, e->stream));
             e->launches += e->graph_kernels[prec][impl];
+        } else if (graph) {
+            // fewer than `chunk` iterations: the one-iteration graph, c times
+            cudaGraphExec_t g;
+            BDC_TRY(get_graph(e, prec, impl, &g, true));
+            for (int i = 0; i < c; i++) {
+                BDC_CUDA_TRY(cudaGraphLaunch(g, e->stream));
+                e->launches += e->graph1_kernels[prec][impl];
+            }
         } else {
             for (int i = 0; i < c; i++) BDC_TRY(iter_once(e, prec, impl));
         }
@@ -1214,11 +1236,7 @@ static bdc_status autotune_impl(bdc_engine *e, PrecBuf<T> &b, int prec, int reps
         }
     }
     b.s = best;
-    for (int impl = 0; impl < 2; impl++)
-        if (e->graph[prec][impl]) {
-            cudaGraphExecDestroy(e->graph[prec][impl]);
-            e->graph[prec][impl] = nullptr;
-        }
+    drop_graphs_prec(e, prec);
     if (best_ms) *best_ms = best_t;
     return BDC_OK;
 }
@@ -1239,11 +1257,7 @@ extern "C" bdc_status bdc_autotune(bdc_engine *e, int prec, int reps, int n2, in
         PrecBuf<double> &d = e->f64;
         if (prec == BDC_FP32) f.s = s;
         else d.s = s;
-        for (int impl = 0; impl < 2; impl++)
-            if (e->graph[prec][impl]) {
-                cudaGraphExecDestroy(e->graph[prec][impl]);
-                e->graph[prec][impl] = nullptr;
-            }
+        drop_graphs_prec(e, prec);
         if (best_ms) *best_ms = 0.0;
         return BDC_OK;
     }

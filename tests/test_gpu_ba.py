@@ -478,3 +478,23 @@ def test_combine_split_boundaries_fp32(n2):
     assert np.all(np.abs(la - lb) <= 2e-5 * np.abs(lb)) and np.all(np.abs(ua - ub) <= 2e-5 * np.abs(ub))
     a.close()
     b.close()
+
+
+def test_short_calls_replay_the_one_iteration_graph():
+    # calls of fewer iterations than a graph chunk replay a one-iteration graph;
+    # any mix of call lengths gives the same iterations, bit for bit, as
+    # launching every kernel on the stream
+    import paper_2604_05867_b300 as bdc
+    n, d = 16, 0.5
+    a = bdc.Engine(n, [d], options=bdc.default_options(chunk=4))
+    b = bdc.Engine(n, [d], options=bdc.default_options(chunk=4, use_graph=0))
+    a.prepare("fp32", "sweep")
+    for c in (1, 3, 4, 1, 6, 2):
+        a.iterate(c, -1.0, "fp32", "sweep")
+    b.iterate(17, -1.0, "fp32", "sweep")
+    la, ua = a.history(0)
+    lb, ub = b.history(0)
+    assert len(la) == 17 and np.array_equal(la, lb) and np.array_equal(ua, ub)
+    assert np.array_equal(a.get_p(), b.get_p())
+    a.close()
+    b.close()
