@@ -498,3 +498,25 @@ def test_short_calls_replay_the_one_iteration_graph():
     assert np.array_equal(a.get_p(), b.get_p())
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("n,n2,w", [(20, 8, 4), (21, 10, 8)])
+def test_column_step_with_1024_threads_fp32(n, n2, w):
+    # column tiles of 128 KB (n1 + log2 w = 14) run the column kernels with
+    # 1024 threads, one CTA per SM (the 8-column layout the bench's autotuner
+    # may choose at n = 24): FP32 stepped half-mode iterations against the
+    # all-shared-memory, unstepped, full-mode FP64 kernels
+    import paper_2604_05867_b300 as bdc
+    d, T = 0.55, 3
+    a = bdc.Engine(n, [d], options=bdc.default_options(sched_n2_fp32=n2, sched_w_fp32=w, enable_literal=0))
+    s = a.schedule("fp32")
+    assert (s["n2"], s["width"]) == (n2, w) and (2 << s["n1"]) * w * 4 > 112 * 1024
+    a.iterate(T, -1.0, "fp32", "sweep")
+    b = bdc.Engine(n, [d], options=bdc.default_options(sched_n2_fp64=n2, sched_w_fp64=w, enable_literal=0,
+                                                       use_regsteps=0, fuse_update=0, use_half=0))
+    b.iterate(T, -1.0, "fp64", "sweep")
+    la, ua = a.history(0)
+    lb, ub = b.history(0)
+    assert np.all(np.abs(la - lb) <= 2e-5 * np.abs(lb)) and np.all(np.abs(ua - ub) <= 2e-5 * np.abs(ub))
+    a.close()
+    b.close()
