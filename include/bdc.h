@@ -110,6 +110,17 @@ void bdc_default_options(bdc_options *opt);
  * Runs no kernel.  *out is owned by the caller (bdc_destroy). */
 bdc_status bdc_create(int n, const double *d, int nd, const bdc_options *opt, bdc_engine **out);
 
+/* Create an engine for a length-mixture deletion channel: instance z
+ * outputs a length-k subsequence of x, chosen uniformly among the C(n,k)
+ * choices of positions (so W(y|x) = b_k Count(y,x) / C(n,k) for |y| = k),
+ * with k drawn from the distribution b[z][0..n] (host [nb][n+1], finite,
+ * non-negative, positive sum; normalised here, copied).  b = the unit vector
+ * at k is the exact deletion channel BDC_{n,k} of Sec. 2.2 (capacity
+ * C_{n,k}); b_k = C(n,k) d^(n-k) (1-d)^k is BDC_d itself.  Every other call
+ * works as for bdc_create, except that dF/dd of bdc_dual_bound is not
+ * defined (BDC_EINVAL).  Errors: BDC_EINVAL. */
+bdc_status bdc_create_lengths(int n, const double *b, int nb, const bdc_options *opt, bdc_engine **out);
+
 /* Bytes of device workspace the engine needs (0 on NULL). */
 size_t bdc_workspace_bytes(const bdc_engine *eng);
 
@@ -197,13 +208,21 @@ bdc_status bdc_set_p(bdc_engine *eng, const double *p_host);
 /* Output marginal q of the current p, host [nd][2^(n+1)] by code, computed in
  * the given precision. */
 bdc_status bdc_get_q(bdc_engine *eng, int precision, double *q_host);
+/* Output marginal q of the current p computed by the literal path (FP64:
+ * for each output class representative y, the sum over its supersequences
+ * x of p(x) Count(y,x), Sec. 5 and Appendix A), host [nd][2^(n+1)] by code,
+ * normalised like bdc_get_q.  Needs enable_literal and an orbit-invariant p
+ * (else BDC_EINVAL).  Switches the engine to the literal representation of
+ * p, like a literal iteration. */
+bdc_status bdc_get_q_literal(bdc_engine *eng, double *q_host);
 /* d-free precompute of representative r (0 <= r < number of reps): its
  * input string, orbit size, N_{x,k} and S_k for k = 0..n (host arrays of
  * n+1). */
 bdc_status bdc_get_rep_stats(bdc_engine *eng, int64_t r, uint64_t *x, int *orbit, uint64_t *N_k, double *S_k);
 /* Number of orbit representatives of {0,1}^n. */
 int64_t bdc_num_reps(const bdc_engine *eng);
-/* Save / restore p and the iteration count to a file (binary). */
+/* Save / restore p and the iteration count to a file (binary; the channel,
+ * d values or length weights, is stored and must match on load). */
 bdc_status bdc_save(bdc_engine *eng, const char *path);
 bdc_status bdc_load(bdc_engine *eng, const char *path);
 
@@ -229,6 +248,15 @@ bdc_status bdc_dual_bound(bdc_engine *eng, int inst, const void *theta_dev, doub
  * certify an optimised q with bdc_certify_upper (one instance: pass a
  * q_dev of nd rows when nd > 1).  theta_dev as in bdc_dual_bound. */
 bdc_status bdc_softmax_classes(bdc_engine *eng, int inst, const void *theta_dev, int precision, double *q_dev);
+
+/* Logits of an output distribution over classes: theta_dev[r] = ln max(q(c_r),
+ * floor) for the representative code c_r of every output class r (q_dev:
+ * device doubles [2^(n+1)] by code, orbit-invariant and normalised; theta_dev:
+ * device array of num_output_classes in `precision`).  softmax over classes
+ * of the result is q again (the inverse of bdc_softmax_classes), e.g. to
+ * start the dual-bound optimisation from a BA output marginal.  Synchronous.
+ * Errors: BDC_EINVAL, BDC_ECUDA. */
+bdc_status bdc_class_logits(bdc_engine *eng, const double *q_dev, double floor, int precision, void *theta_dev);
 
 /* --- measurement --------------------------------------------------------- */
 
@@ -286,6 +314,27 @@ bdc_status bdc_subseq_counts(int n, const uint64_t *x_dev, int64_t nx, uint64_t 
  * set-up (looks up the array's address, sets shared-memory limits) and must
  * come before any stream capture.  n > 18 or bad arguments: BDC_EINVAL. */
 bdc_status bdc_output_marginal_static(int n, double d, const double *p_dev, double *q_dev, void *cuda_stream);
+
+/* --- bound post-processing (host only, Sec. 6) ----------------------------- */
+
+/* Lemma prob-vs-exact (Sec. 2.2): *Cn_d = sum_{k=1}^n C(n,k) d^(n-k)
+ * (1-d)^k Cnk[k], an upper bound on C_n(d) when Cnk[k] >= C_{n,k} (host
+ * array of n+1, index k; Cnk[0] unused).  Long double sum of non-negative
+ * terms, rounded up.  1 <= n <= 64, 0 <= d <= 1.  Errors: BDC_EINVAL. */
+bdc_status bdc_bound_prob_vs_exact(int n, double d, const double *Cnk, double *Cn_d);
+
+/* Lemma worse-UB (Sec. 6): *Cnk = sum_{i=0}^s C(s,i) C(n-s,k-i) / C(n,k)
+ * (Cs[i] + Cns[k-i]), an upper bound on C_{n,k} when Cs[i] >= C_{s,i}
+ * (host [s+1]) and Cns[j] >= C_{n-s,j} (host [n-s+1]).  Terms with k-i
+ * outside [0, n-s] have weight 0.  Rounded up.  2 <= n <= 64, 0 <= k <= n,
+ * 1 <= s < n.  Errors: BDC_EINVAL. */
+bdc_status bdc_bound_split(int n, int k, int s, const double *Cs, const double *Cns, double *Cnk);
+
+/* Lemma convex (Sec. 6, Rahmati and Duman): C(d)/(1-d) <= C(d')/(1-d') for
+ * every d in [d', 1].  From an upper bound C_dp on C(d'), writes *Cd >= C(d)
+ * and *ratio >= C(d')/(1-d') (either may be NULL), rounded up.
+ * Errors: BDC_EINVAL (d' outside [0,1), d outside [d',1], C_dp < 0). */
+bdc_status bdc_bound_high_noise(double d_prime, double C_dp, double d, double *Cd, double *ratio);
 
 /* Thread-local message of the last failing call on this thread. */
 const char *bdc_last_error(void);

@@ -70,7 +70,12 @@ def lib():
                 "orc_recsuperseq": (_u64, [_u64, _int, _int, _u64, _int]),
                 "orc_orbit_rep": (_u64, [_u64, _int, _P]),
                 "orc_dual_bound": (_dbl, [_int, _dbl, _dbl, _P, _P, _i64, _P, _P]),
-                "orc_D_list": (_i64, [_int, _dbl, _P, _P, _i64, _P]),
+                "orc_D_list": (None, [_int, _dbl, _P, _P, _i64, _P]),
+                "orc_pairs_list": (_i64, [_int, _P, _i64]),
+                "orc_set_threads": (_int, [_int]),
+                "orc_sweep_forward": (None, [_int, _dbl, _dbl, _P, _P]),
+                "orc_sweep_adjoint": (None, [_int, _dbl, _dbl, _P, _P]),
+                "orc_subseq_S_list": (None, [_int, _P, _i64, _P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -150,13 +155,26 @@ def D_full(n: int, d: float, q: np.ndarray) -> np.ndarray:
     return D
 
 
-def D_list(n: int, d: float, q: np.ndarray, xs: np.ndarray):
-    """D_x for the given inputs (OpenMP); returns (D, pairs enumerated)."""
+def D_list(n: int, d: float, q: np.ndarray, xs: np.ndarray) -> np.ndarray:
+    """D_x for the given inputs (OpenMP over the list)."""
     q = np.ascontiguousarray(q, np.float64)
     xs = np.ascontiguousarray(xs, np.uint64)
     D = np.zeros(len(xs), np.float64)
-    pairs = lib().orc_D_list(n, float(d), _ptr(q), _ptr(xs), len(xs), _ptr(D))
-    return D, int(pairs)
+    lib().orc_D_list(n, float(d), _ptr(q), _ptr(xs), len(xs), _ptr(D))
+    return D
+
+
+def pairs_list(n: int, xs: np.ndarray) -> int:
+    """Number of (x, distinct y) pairs, the empty output included, that the
+    divergence walk over these inputs enumerates."""
+    xs = np.ascontiguousarray(xs, np.uint64)
+    return int(lib().orc_pairs_list(n, _ptr(xs), len(xs)))
+
+
+def set_threads(t: int) -> int:
+    """Threads of the oracle's OpenMP loops (t <= 0 keeps the current
+    setting); returns the number in use."""
+    return int(lib().orc_set_threads(int(t)))
 
 
 def certify(n: int, d: float, q: np.ndarray):
@@ -275,3 +293,97 @@ def dual_bound(n: int, d: float, tau: float, theta: np.ndarray, cls: np.ndarray,
     F = lib().orc_dual_bound(n, float(d), float(tau), _ptr(theta), _ptr(cls), len(theta),
                              _ptr(g) if grad else None, _ptr(gd))
     return float(F), g, float(gd[0])
+
+
+# --------------------------------------------------------------------------
+# O2: factorised sweep (plain FP64; pinned against the definitions above)
+# --------------------------------------------------------------------------
+def sweep_q(n: int, d: float, p: np.ndarray, counts: bool = False) -> np.ndarray:
+    """q(y) = sum_x p(x) W(y|x) by the prefix recursion (O2).  counts=True
+    uses the embedding counts instead of W: sum_x p(x) Count(y, x)."""
+    p = np.ascontiguousarray(p, np.float64)
+    q = np.zeros(1 << (n + 1), np.float64)
+    a, c = (1.0, 1.0) if counts else (float(d), 1.0 - float(d))
+    lib().orc_sweep_forward(n, a, c, _ptr(p), _ptr(q))
+    return q
+
+
+def sweep_G(n: int, d: float, L: np.ndarray, counts: bool = False) -> np.ndarray:
+    """G(x) = sum_y W(y|x) L(y) (or sum_y Count(y,x) L(y) with counts=True)
+    by the transposed recursion (O2)."""
+    L = np.ascontiguousarray(L, np.float64)
+    G = np.zeros(1 << n, np.float64)
+    a, c = (1.0, 1.0) if counts else (float(d), 1.0 - float(d))
+    lib().orc_sweep_adjoint(n, a, c, _ptr(L), _ptr(G))
+    return G
+
+
+def orbit_reps(n: int):
+    """(reps, rep_index): the orbit representatives of {0,1}^n under
+    complement and reversal (the smallest member, Appendix A) in increasing
+    order, and for every x the index of its orbit's representative."""
+    x = np.arange(1 << n, dtype=np.int64)
+    r = np.zeros_like(x)
+    for i in range(n):
+        r |= ((x >> i) & 1) << (n - 1 - i)
+    full = (1 << n) - 1
+    rep = np.minimum(np.minimum(x, x ^ full), np.minimum(r, r ^ full))
+    reps = np.unique(rep)
+    return reps, np.searchsorted(reps, rep)
+
+
+def subseq_S_all(n: int) -> np.ndarray:
+    """S_k(x) = sum_{|y|=k} Count log2 Count for every x, [2^n][n+1]: the
+    trie walk on orbit representatives (OpenMP), copied to every member of
+    the orbit (Count is preserved by complement and reversal)."""
+    reps, idx = orbit_reps(n)
+    xs = np.ascontiguousarray(reps, np.uint64)
+    S = np.zeros((len(xs), n + 1), np.float64)
+    lib().orc_subseq_S_list(n, _ptr(xs), len(xs), _ptr(S))
+    return S[idx]
+
+
+def keep_weights(n: int, d: float) -> np.ndarray:
+    """omega_k = d^(n-k) (1-d)^k, the probability of one keep pattern of
+    weight k (0^0 = 1)."""
+    k = np.arange(n + 1, dtype=np.float64)
+    return np.power(float(d), n - k) * np.power(1.0 - float(d), k)
+
+
+def neg_entropy_rows(n: int, d: float, S: np.ndarray) -> np.ndarray:
+    """sum_y W(y|x) log2 W(y|x) for every x from S (rows of S per x):
+    sum_k omega_k (S_k(x) + C(n,k) log2 omega_k), terms with omega_k = 0
+    dropped (0 log 0 = 0)."""
+    from math import comb
+    w = keep_weights(n, d)
+    out = np.zeros(S.shape[0], np.float64)
+    for k in range(n + 1):
+        if w[k] > 0.0:
+            out += w[k] * (S[:, k] + comb(n, k) * np.log2(w[k]))
+    return out
+
+
+def D_sweep(n: int, d: float, q: np.ndarray, S: np.ndarray) -> np.ndarray:
+    """D_x = sum_y W log2 W - sum_y W log2 q(y) for every x (O2): the first
+    term from S, the second by the transposed recursion."""
+    with np.errstate(divide="ignore"):
+        L = np.where(q > 0.0, np.log2(np.where(q > 0.0, q, 1.0)), 0.0)
+    L[0] = 0.0
+    return neg_entropy_rows(n, d, S) - sweep_G(n, d, L)
+
+
+def ba_sweep(n: int, d: float, T: int, p0=None, S=None):
+    """T Blahut-Arimoto iterations (Sec. 2.3) with q and D from O2; per
+    iteration t the bounds of X^(t) (lower = log2 sum p 2^D, upper = max D);
+    p is the final X.  S: subseq_S_all(n), computed if not given."""
+    if S is None:
+        S = subseq_S_all(n)
+    p = np.full(1 << n, 1.0 / (1 << n)) if p0 is None else np.array(p0, np.float64, copy=True)
+    lo, up = [], []
+    for _ in range(T):
+        D = D_sweep(n, d, sweep_q(n, d, p), S)
+        Z = float(np.sum(p * np.exp2(D)))
+        lo.append(np.log2(Z))
+        up.append(float(D.max()))
+        p = p * np.exp2(D) / Z
+    return dict(p=p, lower=np.array(lo), upper=np.array(up), iters=T)

@@ -220,16 +220,32 @@ void orc_D_full(int n, double d, const double *q, double *D) {
     for (int64_t x = 0; x < nx; x++) D[x] = orc_D_point(n, d, q, (uint64_t)x);
 }
 
-/* D_x for a list of inputs (OpenMP over the list); returns the number of
- * (x, distinct y) pairs enumerated.  Used to time the oracle on a sample. */
-int64_t orc_D_list(int n, double d, const double *q, const uint64_t *xs, int64_t count, double *D) {
+/* D_x for a list of inputs (OpenMP over the list).  Used to time the oracle
+ * on a sample (orc_pairs_list counts the pairs it enumerates, separately). */
+void orc_D_list(int n, double d, const double *q, const uint64_t *xs, int64_t count, double *D) {
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t i = 0; i < count; i++) D[i] = orc_D_point(n, d, q, xs[i]);
+}
+
+/* Number of (x, distinct y) pairs, the empty output included, over a list
+ * of inputs (OpenMP). */
+int64_t orc_pairs_list(int n, const uint64_t *xs, int64_t count) {
     int64_t pairs = 0;
 #pragma omp parallel for schedule(dynamic, 4) reduction(+ : pairs)
-    for (int64_t i = 0; i < count; i++) {
-        D[i] = orc_D_point(n, d, q, xs[i]);
-        pairs += orc_subseq_list(n, xs[i], NULL, NULL) + 1;
-    }
+    for (int64_t i = 0; i < count; i++) pairs += orc_subseq_list(n, xs[i], NULL, NULL) + 1;
     return pairs;
+}
+
+/* Threads of the OpenMP loops (<= 0: leave the runtime's default); returns
+ * the number the loops will use. */
+int orc_set_threads(int t) {
+#ifdef _OPENMP
+    if (t > 0) omp_set_num_threads(t);
+    return omp_get_max_threads();
+#else
+    (void)t;
+    return 1;
+#endif
 }
 
 /* Dual (minimax) upper bound for any positive q: max_x D(W_x || q/sum q)
@@ -530,4 +546,101 @@ double orc_dual_bound(int n, double d, double tau, const double *theta, const in
     if (grad_d) *grad_d = gd;
     free(q); free(g); free(Dx); free(dD); free(cnt); free(W);
     return F;
+}
+
+/* ---------------------------------------------------------------------------
+ * O2: the factorised sweep in plain FP64 (a second CPU implementation of the
+ * output marginal and of the divergence's cross term, written from the
+ * prefix recursion of the channel rule of Sec. 2.2; no blocking, no fusion).
+ * It is the same-algorithm CPU baseline and the full-iteration reference at
+ * sizes where the definitions above take too long; it is pinned against them
+ * (q_full, D_full, embed_count) by the -m "not gpu" tests.
+ *
+ * Read x = r s left to right, r the first i symbols, s the other n - i.
+ * W_i(u|r) is the probability that the first i symbols leave u; appending b
+ * to r either deletes b (weight a) or keeps it, matched to u's last symbol
+ * (weight c):  W_{i+1}(u | r b) = a W_i(u|r) + c [u ends in b] W_i(u^-|r),
+ * with u^- = u without its last symbol.  For BDC_d, (a, c) = (d, 1 - d);
+ * with (a, c) = (1, 1) the recursion counts embeddings (Count(u, r)).  The
+ * partial sums F_i(u, s) = sum_r p(r s) W_i(u|r) then obey
+ *     F_{i+1}(u, s') = a (F_i(u, 0 s') + F_i(u, 1 s')) + c F_i(u^-, u_last s')
+ * from F_0(empty, x) = p(x) to F_n(u, empty) = sum_x p(x) W(u|x) = q(u).
+ * Level i stores F_i(u, s) at index (code(u) << (n - i)) | s, code(u) =
+ * (1 << |u|) | u, so every level lives in [1, 2^(n+1)).
+ * The transpose runs the other way: from Gbar_n(u) = L(u),
+ *     Gbar_i(v, b s') = a Gbar_{i+1}(v, s') + c Gbar_{i+1}(v b, s'),
+ * and Gbar_0(empty, x) = sum_y W(y|x) L(y).
+ * ------------------------------------------------------------------------- */
+static int bitlen_u64(uint64_t v) { return v ? 64 - __builtin_clzll(v) : 0; }
+
+/* q[c] = sum_x p(x) W(y|x) over all codes (slot 0 = 0). */
+void orc_sweep_forward(int n, double a, double c, const double *p, double *q) {
+    uint64_t M = 1ull << (n + 1);
+    double *cur = (double *)calloc(M, sizeof(double));
+    double *nxt = (double *)calloc(M, sizeof(double));
+    for (uint64_t x = 0; x < (1ull << n); x++) cur[(1ull << n) | x] = p[x];
+    for (int i = 0; i < n; i++) {
+        int rest = n - i - 1; /* length of s' */
+        uint64_t ncodes = 1ull << (i + 2); /* u of length 0 .. i+1 */
+        memset(nxt, 0, M * sizeof(double));
+#pragma omp parallel for schedule(static)
+        for (int64_t cu = 1; cu < (int64_t)ncodes; cu++) {
+            int k = bitlen_u64((uint64_t)cu) - 1;
+            for (uint64_t s = 0; s < (1ull << rest); s++) {
+                double v = 0.0;
+                if (k <= i) {
+                    uint64_t base = ((uint64_t)cu << (rest + 1)) | s;
+                    v += a * (cur[base] + cur[base | (1ull << rest)]);
+                }
+                if (k >= 1) {
+                    uint64_t b = (uint64_t)cu & 1u, cp = (uint64_t)cu >> 1;
+                    v += c * cur[(cp << (rest + 1)) | (b << rest) | s];
+                }
+                nxt[((uint64_t)cu << rest) | s] = v;
+            }
+        }
+        double *t = cur; cur = nxt; nxt = t;
+    }
+    memcpy(q, cur, M * sizeof(double));
+    q[0] = 0.0;
+    free(cur);
+    free(nxt);
+}
+
+/* G[x] = sum_y W(y|x) L[code(y)] for every x (L indexed by code, slot 0
+ * ignored). */
+void orc_sweep_adjoint(int n, double a, double c, const double *L, double *G) {
+    uint64_t M = 1ull << (n + 1);
+    double *cur = (double *)calloc(M, sizeof(double));
+    double *nxt = (double *)calloc(M, sizeof(double));
+    memcpy(cur, L, M * sizeof(double));
+    cur[0] = 0.0;
+    for (int i = n - 1; i >= 0; i--) {
+        int rest = n - i - 1;
+        uint64_t nv = 1ull << (i + 1); /* v of length 0 .. i */
+        memset(nxt, 0, M * sizeof(double));
+#pragma omp parallel for schedule(static)
+        for (int64_t cv = 1; cv < (int64_t)nv; cv++) {
+            for (uint64_t b = 0; b < 2; b++)
+                for (uint64_t s = 0; s < (1ull << rest); s++) {
+                    double v = a * cur[((uint64_t)cv << rest) | s] + c * cur[((((uint64_t)cv << 1) | b) << rest) | s];
+                    nxt[((uint64_t)cv << (rest + 1)) | (b << rest) | s] = v;
+                }
+        }
+        double *t = cur; cur = nxt; nxt = t;
+    }
+    for (uint64_t x = 0; x < (1ull << n); x++) G[x] = cur[(1ull << n) | x];
+    free(cur);
+    free(nxt);
+}
+
+/* S_k(x) = sum over distinct length-k subsequences y of x of
+ * Count(y,x) log2 Count(y,x), for a list of inputs (OpenMP over the list);
+ * S is [count][n+1]. */
+void orc_subseq_S_list(int n, const uint64_t *xs, int64_t count, double *S) {
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < count; i++) {
+        uint64_t N[ORC_MAXN + 1], sc[ORC_MAXN + 1];
+        orc_subseq_stats(n, xs[i], N, S + (size_t)i * (n + 1), sc);
+    }
 }

@@ -61,6 +61,7 @@ def lib():
         sig = {
             "bdc_default_options": (None, [P]),
             "bdc_create": (I, [I, P, I, P, P]),
+            "bdc_create_lengths": (I, [I, P, I, P, P]),
             "bdc_workspace_bytes": (SZ, [P]),
             "bdc_bind": (I, [P, P, SZ, P]),
             "bdc_destroy": (None, [P]),
@@ -72,6 +73,7 @@ def lib():
             "bdc_get_p": (I, [P, P]),
             "bdc_set_p": (I, [P, P]),
             "bdc_get_q": (I, [P, I, P]),
+            "bdc_get_q_literal": (I, [P, P]),
             "bdc_get_rep_stats": (I, [P, I64, P, P, P, P]),
             "bdc_num_reps": (I64, [P]),
             "bdc_save": (I, [P, ctypes.c_char_p]),
@@ -82,6 +84,7 @@ def lib():
             "bdc_subseq_counts": (I, [I, P, I64, P, P, P, P]),
             "bdc_launch_count": (I64, [P]),
             "bdc_softmax_classes": (I, [P, I, P, I, P]),
+            "bdc_class_logits": (I, [P, P, D, I, P]),
             "bdc_batch_create": (I, [P, I, I, P]),
             "bdc_get_schedule": (I, [P, I, P, P, P]),
             "bdc_autotune": (I, [P, I, I, I, I, P]),
@@ -128,19 +131,34 @@ class Engine:
     The workspace is a torch uint8 CUDA tensor owned by this object; the
     engine runs all its kernels on ``stream`` (default: the current stream at
     construction).  ``bdc_bind`` runs the d-free precompute synchronously.
+
+    ``lengths`` (an array [nb, n+1], instead of ``ds``) makes a
+    length-mixture channel per row (bdc_create_lengths): a one-hot row at k
+    is the exact deletion channel BDC_{n,k}.
     """
 
-    def __init__(self, n: int, ds: Sequence[float], options: Optional[Options] = None, device=None, stream=None):
+    def __init__(self, n: int, ds: Sequence[float] = (), options: Optional[Options] = None, device=None,
+                 stream=None, lengths=None):
         import torch
         self.n = int(n)
-        self.ds = [float(v) for v in ds]
-        self.nd = len(self.ds)
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         L = lib()
-        darr = (ctypes.c_double * self.nd)(*self.ds)
         h = ctypes.c_void_p()
-        _check(L.bdc_create(self.n, ctypes.cast(darr, ctypes.c_void_p), self.nd,
-                            ctypes.byref(options) if options is not None else None, ctypes.byref(h)))
+        opt = ctypes.byref(options) if options is not None else None
+        if lengths is not None:
+            b = np.ascontiguousarray(np.atleast_2d(lengths), np.float64)
+            if b.shape[1] != self.n + 1:
+                raise ValueError("lengths must have n+1 columns")
+            self.lengths = b
+            self.ds = [float("nan")] * b.shape[0]
+            self.nd = b.shape[0]
+            _check(L.bdc_create_lengths(self.n, _np_ptr(b), self.nd, opt, ctypes.byref(h)))
+        else:
+            self.lengths = None
+            self.ds = [float(v) for v in ds]
+            self.nd = len(self.ds)
+            darr = (ctypes.c_double * self.nd)(*self.ds)
+            _check(L.bdc_create(self.n, ctypes.cast(darr, ctypes.c_void_p), self.nd, opt, ctypes.byref(h)))
         self._h = h
         self.ws_bytes = int(L.bdc_workspace_bytes(h))
         with torch.cuda.device(self.device):
@@ -284,6 +302,13 @@ class Engine:
         _check(lib().bdc_get_q(self._h, _PREC[precision], _np_ptr(q)))
         return q
 
+    def get_q_literal(self) -> np.ndarray:
+        """Output marginal of the current p by the literal (supersequence
+        enumeration) path, FP64, host [nd, 2^(n+1)] by code."""
+        q = np.zeros((self.nd, 2 << self.n))
+        _check(lib().bdc_get_q_literal(self._h, _np_ptr(q)))
+        return q
+
     def rep_stats(self, r: int):
         x = ctypes.c_uint64(0)
         o = ctypes.c_int(0)
@@ -304,12 +329,16 @@ class Engine:
         _check(lib().bdc_load(self._h, path.encode()))
 
     # -- smoothed dual bound -------------------------------------------------------
-    def dual_bound(self, inst: int, theta, tau: float, precision="fp64", grad: bool = True):
-        """(F, max_D, grad_theta tensor or None, dF/dd or None) for instance inst."""
+    def dual_bound(self, inst: int, theta, tau: float, precision="fp64", grad: bool = True,
+                   grad_d: Optional[bool] = None):
+        """(F, max_D, grad_theta tensor or None, dF/dd or None) for instance inst.
+        grad_d defaults to grad (dF/dd exists for BDC_d instances only)."""
         import torch
         want = torch.float32 if _PREC[precision] == FP32 else torch.float64
         assert theta.dtype == want and theta.is_cuda and theta.is_contiguous()
         assert theta.numel() == self.num_output_classes
+        if grad_d is None:
+            grad_d = grad
         F = ctypes.c_double(0)
         mD = ctypes.c_double(0)
         gd = ctypes.c_double(0)
@@ -317,8 +346,23 @@ class Engine:
         _check(lib().bdc_dual_bound(self._h, int(inst), ctypes.c_void_p(theta.data_ptr()), float(tau),
                                     _PREC[precision], ctypes.byref(F), ctypes.byref(mD),
                                     ctypes.c_void_p(g.data_ptr()) if grad else None,
-                                    ctypes.byref(gd) if grad else None))
-        return F.value, mD.value, g, (gd.value if grad else None)
+                                    ctypes.byref(gd) if grad_d else None))
+        return F.value, mD.value, g, (gd.value if grad_d else None)
+
+    def class_logits(self, q, precision="fp64", floor: float = 1e-300):
+        """Logits over output classes whose softmax is q (bdc_class_logits);
+        q: host array or CUDA tensor of 2^(n+1) doubles by code."""
+        import torch
+        qd = torch.as_tensor(np.asarray(q) if not torch.is_tensor(q) else q, dtype=torch.float64,
+                             device=self.device).contiguous()
+        assert qd.numel() == 2 << self.n
+        want = torch.float32 if _PREC[precision] == FP32 else torch.float64
+        th = torch.empty(self.num_output_classes, dtype=want, device=self.device)
+        with torch.cuda.device(self.device):
+            torch.cuda.current_stream().synchronize()
+        _check(lib().bdc_class_logits(self._h, ctypes.c_void_p(qd.data_ptr()), float(floor), _PREC[precision],
+                                      ctypes.c_void_p(th.data_ptr())))
+        return th
 
 
     def softmax_classes(self, inst: int, theta, precision="fp64"):

@@ -41,8 +41,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OBJ, exist_ok=True)
     objs = []
 
+    headers = [f for f in _deps() if not f.endswith(".cu")]
+    newest_header = max(os.path.getmtime(f) for f in headers)
+
     def compile_one(src):
         obj = os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
+        if (not force and os.path.exists(obj) and os.path.getmtime(obj) >= os.path.getmtime(src)
+                and os.path.getmtime(obj) >= newest_header):
+            return obj  # up to date: its source and every header are older
         cmd = [NVCC, *ARCH, *FLAGS, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:

@@ -104,7 +104,10 @@ struct PrecBuf {
 
 struct bdc_engine {
     int n = 0, nd = 0;
-    std::vector<double> d;
+    std::vector<double> d;     // deletion probability per instance (NaN for a length-mixture channel)
+    // Length-mixture channels (bdc_create_lengths): per instance the
+    // distribution b_k of the output length, [nd][n+1]; empty for BDC_d.
+    std::vector<double> blen;
     bdc_options opt;
     size_t ws_bytes = 0;
     char *ws = nullptr;

@@ -250,7 +250,7 @@ extern "C" bdc_status bdc_dual_bound(bdc_engine *e, int inst, const void *theta_
         return BDC_EINVAL;
     }
     if (grad_d && !(e->d[inst] > 0.0 && e->d[inst] < 1.0)) {
-        bdc_set_error("bdc_dual_bound: dF/dd needs 0 < d < 1");
+        bdc_set_error("bdc_dual_bound: dF/dd needs a BDC_d instance with 0 < d < 1 (not a length mixture)");
         return BDC_EINVAL;
     }
     if (prec == BDC_FP32)
@@ -258,4 +258,41 @@ extern "C" bdc_status bdc_dual_bound(bdc_engine *e, int inst, const void *theta_
                                 grad_d);
     return dual_impl<double>(e, e->f64, inst, (const double *)theta_dev, tau, F, max_D, (double *)grad_theta_dev,
                              grad_d);
+}
+
+namespace {
+
+// theta[r] = ln max(q(rep_r), floor): logits whose softmax over classes is q
+// for an orbit-invariant q normalised to 1 (the inverse of the expansion)
+template <typename T>
+__global__ void k_class_logits(int64_t Rout, const uint32_t *oreps, const double *q, double floor_v, T *theta) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < Rout; r += (int64_t)gridDim.x * blockDim.x)
+        theta[r] = (T)log(fmax(q[oreps[r]], floor_v));
+}
+
+}  // namespace
+
+extern "C" bdc_status bdc_class_logits(bdc_engine *e, const double *q_dev, double floor_v, int prec,
+                                       void *theta_dev) {
+    if (!e || !e->bound) {
+        bdc_set_error("bdc_class_logits: no workspace bound");
+        return BDC_ENOTBOUND;
+    }
+    if (!q_dev || !theta_dev || !(floor_v > 0.0) || (prec != BDC_FP32 && prec != BDC_FP64)) {
+        bdc_set_error("bdc_class_logits: bad arguments (q, theta, floor > 0, precision)");
+        return BDC_EINVAL;
+    }
+    const int g = (int)std::min<int64_t>((e->Rout + RT - 1) / RT, 4096);
+    if (prec == BDC_FP32)
+        k_class_logits<float><<<g, RT, 0, e->stream>>>(e->Rout, e->oreps, q_dev, floor_v, (float *)theta_dev);
+    else
+        k_class_logits<double><<<g, RT, 0, e->stream>>>(e->Rout, e->oreps, q_dev, floor_v, (double *)theta_dev);
+    e->launches++;
+    cudaError_t err = cudaGetLastError();
+    if (err == cudaSuccess) err = cudaStreamSynchronize(e->stream);
+    if (err != cudaSuccess) {
+        bdc_set_error(std::string("bdc_class_logits: ") + cudaGetErrorString(err));
+        return BDC_ECUDA;
+    }
+    return BDC_OK;
 }

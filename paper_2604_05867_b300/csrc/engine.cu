@@ -243,6 +243,8 @@ extern "C" void bdc_default_options(bdc_options *o) {
     o->use_tma = 0;
 }
 
+static bdc_engine *new_engine(int n, int nd, const bdc_options *opt);
+
 extern "C" bdc_status bdc_create(int n, const double *d, int nd, const bdc_options *opt, bdc_engine **out) {
     if (!out) BDC_FAIL(BDC_EINVAL, "bdc_create: out is NULL");
     *out = nullptr;
@@ -250,10 +252,40 @@ extern "C" bdc_status bdc_create(int n, const double *d, int nd, const bdc_optio
     if (!d || nd < 1 || nd > 4096) BDC_FAIL(BDC_EINVAL, "bdc_create: need 1 <= nd <= 4096 values of d");
     for (int i = 0; i < nd; i++)
         if (!(d[i] >= 0.0 && d[i] <= 1.0)) BDC_FAIL(BDC_EINVAL, "bdc_create: every d must lie in [0, 1]");
+    bdc_engine *e = new_engine(n, nd, opt);
+    e->d.assign(d, d + nd);
+    *out = e;
+    return BDC_OK;
+}
+
+extern "C" bdc_status bdc_create_lengths(int n, const double *b, int nb, const bdc_options *opt, bdc_engine **out) {
+    if (!out) BDC_FAIL(BDC_EINVAL, "bdc_create_lengths: out is NULL");
+    *out = nullptr;
+    if (n < 1 || n > BDC_MAXN) BDC_FAIL(BDC_EINVAL, "bdc_create_lengths: n must be in [1, 26]");
+    if (!b || nb < 1 || nb > 4096) BDC_FAIL(BDC_EINVAL, "bdc_create_lengths: need 1 <= nb <= 4096 length distributions");
+    std::vector<double> bl((size_t)nb * (n + 1));
+    for (int z = 0; z < nb; z++) {
+        long double s = 0.0L;
+        for (int k = 0; k <= n; k++) {
+            double v = b[(size_t)z * (n + 1) + k];
+            if (!(v >= 0.0) || !std::isfinite(v))
+                BDC_FAIL(BDC_EINVAL, "bdc_create_lengths: every b_k must be finite and non-negative");
+            s += v;
+        }
+        if (!(s > 0.0L)) BDC_FAIL(BDC_EINVAL, "bdc_create_lengths: every length distribution needs a positive sum");
+        for (int k = 0; k <= n; k++) bl[(size_t)z * (n + 1) + k] = (double)(b[(size_t)z * (n + 1) + k] / s);
+    }
+    bdc_engine *e = new_engine(n, nb, opt);
+    e->d.assign(nb, std::nan(""));
+    e->blen = bl;
+    *out = e;
+    return BDC_OK;
+}
+
+static bdc_engine *new_engine(int n, int nd, const bdc_options *opt) {
     bdc_engine *e = new bdc_engine();
     e->n = n;
     e->nd = nd;
-    e->d.assign(d, d + nd);
     if (opt) e->opt = *opt;
     else bdc_default_options(&e->opt);
     if (e->opt.chunk < 1) e->opt.chunk = 1;
@@ -263,8 +295,7 @@ extern "C" bdc_status bdc_create(int n, const double *d, int nd, const bdc_optio
     e->f32.s = make_sched(n, 4, e->opt.sched_n2_fp32, e->opt.sched_w_fp32);
     e->f64.s = make_sched(n, 8, e->opt.sched_n2_fp64, e->opt.sched_w_fp64);
     e->ws_bytes = carve(e, nullptr);
-    *out = e;
-    return BDC_OK;
+    return e;
 }
 
 extern "C" size_t bdc_workspace_bytes(const bdc_engine *e) { return e ? e->ws_bytes : 0; }
@@ -317,14 +348,18 @@ extern "C" bdc_status bdc_bind(bdc_engine *e, void *ws, size_t bytes, void *stre
     std::vector<double> bk((size_t)6 * nd * (n + 1), 0.0);
     std::vector<double> rb((size_t)nd * (n + 1), 0.0), rw((size_t)nd * (n + 1), 0.0);
     std::vector<double> inst((size_t)nd * INST_STRIDE, 0.0);
+    const bool lengths = !e->blen.empty();
     for (int z = 0; z < nd; z++) {
-        long double d = e->d[z], dm = 1.0L - d;
+        long double d = lengths ? 0.5L : e->d[z], dm = 1.0L - d;
         double sum_blc = 0.0;
         long double negh = 0.0L, c0 = 0.0L;
         for (int k = 0; k <= n; k++) {
-            long double kw = powl(d, (long double)(n - k)) * powl(dm, (long double)k);
+            // BDC_d: b_k = C(n,k) d^(n-k) (1-d)^k, one keep pattern weighs kw = b_k / C(n,k);
+            // a length mixture (e.g. the exact channel BDC_{n,k}, Sec. 2.2): b_k given
             long double C = (long double)binom_d(n, k);
-            long double b = C * kw;
+            long double kw = lengths ? (long double)e->blen[(size_t)z * (n + 1) + k] / C
+                                     : powl(d, (long double)(n - k)) * powl(dm, (long double)k);
+            long double b = lengths ? (long double)e->blen[(size_t)z * (n + 1) + k] : C * kw;
             size_t o = (size_t)z * (n + 1) + k, S = (size_t)nd * (n + 1);
             bk[o] = (double)b;
             bk[S + o] = (double)kw;
@@ -335,7 +370,7 @@ extern "C" bdc_status bdc_bind(bdc_engine *e, void *ws, size_t bytes, void *stre
             sum_blc += (double)b * (double)log2l(C);
             if (b > 0) negh += b * log2l(b);
             // d-derivative weights: db_k/dd = rho_k b_k, rho_k = (n-k)/d - k/(1-d)
-            if (d > 0 && dm > 0) {
+            if (!lengths && d > 0 && dm > 0) {
                 long double rho = (long double)(n - k) / d - (long double)k / dm;
                 rb[o] = (double)(rho * b);
                 rw[o] = (double)(rho * kw);
@@ -1073,6 +1108,35 @@ extern "C" bdc_status bdc_get_q(bdc_engine *e, int prec, double *q_host) {
     return BDC_OK;
 }
 
+extern "C" bdc_status bdc_get_q_literal(bdc_engine *e, double *q_host) {
+    if (!e || !e->bound) BDC_FAIL(BDC_ENOTBOUND, "bdc_get_q_literal: no workspace bound");
+    if (!q_host) BDC_FAIL(BDC_EINVAL, "bdc_get_q_literal: NULL output");
+    if (!e->opt.enable_literal) BDC_FAIL(BDC_EINVAL, "bdc_get_q_literal: literal path disabled (enable_literal = 0)");
+    if (!e->orbit_ok)
+        BDC_FAIL(BDC_EINVAL, "bdc_get_q_literal: the literal path needs an orbit-invariant p (complement and reversal)");
+    BDC_TRY(make_current(e, 2));
+    BDC_TRY(materialize(e));  // the pending update is applied to every orbit member
+    BDC_TRY(activate(e, -1.0));
+    BDC_TRY(launch_literal_q(e));  // per-length q_k(y) * sum p, every code of every class
+    const int n = e->n, nd = e->nd;
+    const size_t N = (size_t)1 << n, M = (size_t)2 << n;
+    std::vector<double> qk(M * nd), p(N * nd), bk((size_t)nd * (n + 1));
+    BDC_CUDA_TRY(cudaMemcpyAsync(qk.data(), e->lit_q, qk.size() * sizeof(double), cudaMemcpyDeviceToHost, e->stream));
+    BDC_CUDA_TRY(cudaMemcpyAsync(p.data(), e->lit_p, p.size() * sizeof(double), cudaMemcpyDeviceToHost, e->stream));
+    BDC_CUDA_TRY(cudaMemcpyAsync(bk.data(), e->bk, bk.size() * sizeof(double), cudaMemcpyDeviceToHost, e->stream));
+    BDC_TRY(sync_check(e, "bdc_get_q_literal"));
+    for (int z = 0; z < nd; z++) {
+        double s = 0.0;
+        for (size_t x = 0; x < N; x++) s += p[z * N + x];
+        q_host[z * M] = 0.0;
+        for (size_t c = 1; c < M; c++) {
+            int k = 63 - __builtin_clzll((unsigned long long)c);
+            q_host[z * M + c] = bk[(size_t)z * (n + 1) + k] * qk[z * M + c] / s;
+        }
+    }
+    return BDC_OK;
+}
+
 extern "C" int64_t bdc_num_reps(const bdc_engine *e) { return e ? e->R : 0; }
 extern "C" int64_t bdc_num_output_classes(const bdc_engine *e) { return e ? e->Rout : 0; }
 
@@ -1113,11 +1177,15 @@ extern "C" bdc_status bdc_save(bdc_engine *e, const char *path) {
     BDC_TRY(download_p(e, p.data(), false));  // exact device state: resume is bit-identical
     FILE *f = fopen(path, "wb");
     if (!f) BDC_FAIL(BDC_EINVAL, std::string("bdc_save: cannot open ") + path);
-    const char magic[8] = {'B', 'D', 'C', 'B', 'A', '0', '0', '1'};
-    int32_t hdr[2] = {e->n, e->nd};
+    // format 2: magic, {n, nd, channel kind}, the channel (nd values of d, or
+    // nd x (n+1) length weights), iterations, p
+    const char magic[8] = {'B', 'D', 'C', 'B', 'A', '0', '0', '2'};
+    const bool lengths = !e->blen.empty();
+    int32_t hdr[3] = {e->n, e->nd, lengths ? 1 : 0};
+    const std::vector<double> &chan = lengths ? e->blen : e->d;
     int64_t it = e->iters_total;
     bool ok = fwrite(magic, 1, 8, f) == 8 && fwrite(hdr, sizeof hdr, 1, f) == 1 &&
-              fwrite(e->d.data(), sizeof(double), e->nd, f) == (size_t)e->nd && fwrite(&it, sizeof it, 1, f) == 1 &&
+              fwrite(chan.data(), sizeof(double), chan.size(), f) == chan.size() && fwrite(&it, sizeof it, 1, f) == 1 &&
               fwrite(p.data(), sizeof(double), cnt, f) == cnt;
     fclose(f);
     if (!ok) BDC_FAIL(BDC_EINVAL, "bdc_save: write failed");
@@ -1130,19 +1198,21 @@ extern "C" bdc_status bdc_load(bdc_engine *e, const char *path) {
     FILE *f = fopen(path, "rb");
     if (!f) BDC_FAIL(BDC_EINVAL, std::string("bdc_load: cannot open ") + path);
     char magic[8];
-    int32_t hdr[2];
+    int32_t hdr[3];
     int64_t it = 0;
-    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "BDCBA001", 8) == 0 && fread(hdr, sizeof hdr, 1, f) == 1 &&
-              hdr[0] == e->n && hdr[1] == e->nd;
-    std::vector<double> d(e->nd);
+    const bool lengths = !e->blen.empty();
+    const std::vector<double> &chan = lengths ? e->blen : e->d;
+    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "BDCBA002", 8) == 0 && fread(hdr, sizeof hdr, 1, f) == 1 &&
+              hdr[0] == e->n && hdr[1] == e->nd && hdr[2] == (lengths ? 1 : 0);
+    std::vector<double> c(chan.size());
     const size_t N = (size_t)1 << e->n, cnt = N * e->nd;
     std::vector<double> p(cnt);
-    ok = ok && fread(d.data(), sizeof(double), e->nd, f) == (size_t)e->nd && fread(&it, sizeof it, 1, f) == 1 &&
+    ok = ok && fread(c.data(), sizeof(double), c.size(), f) == c.size() && fread(&it, sizeof it, 1, f) == 1 &&
          fread(p.data(), sizeof(double), cnt, f) == cnt;
     fclose(f);
-    if (!ok) BDC_FAIL(BDC_EINVAL, "bdc_load: not a checkpoint of this engine (n, nd) or truncated");
-    for (int z = 0; z < e->nd; z++)
-        if (d[z] != e->d[z]) BDC_FAIL(BDC_EINVAL, "bdc_load: checkpoint has different d values");
+    if (!ok) BDC_FAIL(BDC_EINVAL, "bdc_load: not a checkpoint of this engine (n, nd, channel kind) or truncated");
+    if (memcmp(c.data(), chan.data(), c.size() * sizeof(double)) != 0)
+        BDC_FAIL(BDC_EINVAL, "bdc_load: checkpoint has a different channel (d values or length weights)");
     BDC_TRY(upload_p(e, p.data(), false));
     e->iters_total = it;
     return BDC_OK;

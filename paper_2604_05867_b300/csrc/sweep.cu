@@ -28,7 +28,9 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
+#include <mutex>
 #include <type_traits>
 
 namespace {
@@ -2154,10 +2156,15 @@ __global__ void k_static_init(int n, double d, double *inst, double *wk, double 
     if (t == 0) q_out[0] = 0.0;
 }
 
+// Per-device set-up state.  The set-up runs under a mutex so that two host
+// threads making a device's first call at the same time do it once; later
+// calls read the published address without taking the lock.
 struct StaticDev {
-    double *base = nullptr;
+    std::atomic<double *> base{nullptr};
+    int sms = 0;  // multiprocessor count of the device (grid cap of the combine)
 };
 StaticDev g_static_dev[64];
+std::mutex g_static_mu;
 
 }  // namespace
 
@@ -2178,19 +2185,27 @@ extern "C" bdc_status bdc_output_marginal_static(int n, double d, const double *
         return BDC_EINVAL;
     }
     const Sched s = make_sched(n, 8, 0, 0);
-    if (!g_static_dev[dev].base) {
+    if (!g_static_dev[dev].base.load(std::memory_order_acquire)) {
         // once per device, with that device current
-        void *ptr = nullptr;
-        cudaError_t err = cudaGetSymbolAddress(&ptr, g_static_scratch);
-        if (err != cudaSuccess || !ptr) {
-            bdc_set_error(std::string("bdc_output_marginal_static: cudaGetSymbolAddress: ") + cudaGetErrorString(err));
-            return BDC_ECUDA;
+        std::lock_guard<std::mutex> lock(g_static_mu);
+        if (!g_static_dev[dev].base.load(std::memory_order_relaxed)) {
+            void *ptr = nullptr;
+            cudaError_t err = cudaGetSymbolAddress(&ptr, g_static_scratch);
+            if (err != cudaSuccess || !ptr) {
+                bdc_set_error(std::string("bdc_output_marginal_static: cudaGetSymbolAddress: ") +
+                              cudaGetErrorString(err));
+                return BDC_ECUDA;
+            }
+            int sms = 0;
+            BDC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            const size_t big = (size_t)16384 * sizeof(double);
+            BDC_CUDA_TRY(prepare_all<double>(big, big));
+            g_static_dev[dev].sms = std::max(1, sms);
+            g_static_dev[dev].base.store((double *)ptr, std::memory_order_release);
         }
-        const size_t big = (size_t)16384 * sizeof(double);
-        BDC_CUDA_TRY(prepare_all<double>(big, big));
-        g_static_dev[dev].base = (double *)ptr;
     }
-    double *base = g_static_dev[dev].base;
+    double *base = g_static_dev[dev].base.load(std::memory_order_acquire);
+    const int sms = g_static_dev[dev].sms;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const size_t N = (size_t)1 << n;
     double *inst = base;                       // INST_STRIDE doubles
@@ -2228,7 +2243,7 @@ extern "C" bdc_status bdc_output_marginal_static(int n, double d, const double *
         SW_WITH_R(rmax_fwd<double>(), rr,
                   (k_rows_fwd<double, R, false><<<dim3((2u << s.n1) - 1u, 1), SW_THREADS, tile_bytes_rows<double>(s), st>>>(
                       a, p, F1, Tm, Ts)));
-        int nb = (int)std::min<size_t>((2 * N) / 256 + 1, 148 * 16);
+        int nb = (int)std::min<size_t>((2 * N) / 256 + 1, (size_t)sms * 16);
         k_combine<double, false><<<dim3(nb, 1), 256, 0, st>>>(a, p, F1, Tm, Ts, q_dev, L, MODE_DUAL);
     }
     BDC_CUDA_TRY(cudaGetLastError());

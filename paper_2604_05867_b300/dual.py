@@ -19,32 +19,43 @@ def _torch():
 
 
 class DualBound:
-    """``DualBound.apply(theta, engine, inst, tau, precision) -> F`` (a 0-d
-    tensor on theta's device); backward fills theta.grad.  The last call's
-    dF/dd and max_x D_x are kept in ``DualBound.last``."""
+    """``DualBound.apply(theta, engine, inst, tau, precision, d=None) -> F``
+    (a 0-d tensor on theta's device).  ``d`` is an optional 0-d tensor
+    holding the instance's deletion probability (it must equal the engine's
+    d: the channel is fixed when the engine is built); when it requires
+    grad, backward writes dF/dd (at fixed theta) into d.grad beside
+    theta.grad.  The last call's F, max_x D_x and dF/dd are kept in
+    ``DualBound.last``."""
 
     last = {}
     _fn = None
 
     @classmethod
-    def apply(cls, theta, engine, inst: int = 0, tau: float = 1e-3, precision: str = "fp64"):
+    def apply(cls, theta, engine, inst: int = 0, tau: float = 1e-3, precision: str = "fp64", d=None):
         torch = _torch()
         if cls._fn is None:
             class _F(torch.autograd.Function):
                 @staticmethod
-                def forward(ctx, th, eng, i, t, prec):
-                    F, mD, g, gd = eng.dual_bound(i, th.detach().contiguous(), t, prec, grad=True)
-                    ctx.save_for_backward(g)
+                def forward(ctx, th, dd, eng, i, t, prec):
+                    if float(dd) != eng.ds[i]:
+                        raise ValueError("d must equal the engine's deletion probability of instance %d" % i)
+                    want_d = bool(ctx.needs_input_grad[1])
+                    F, mD, g, gd = eng.dual_bound(i, th.detach().contiguous(), t, prec, grad=True, grad_d=want_d)
+                    ctx.save_for_backward(g, th.new_tensor(gd if want_d else 0.0, dtype=torch.float64))
+                    ctx.d_dtype = dd.dtype
                     DualBound.last = {"F": F, "max_D": mD, "grad_d": gd}
                     return th.new_tensor(F)
 
                 @staticmethod
                 def backward(ctx, gF):
-                    (g,) = ctx.saved_tensors
-                    return gF * g, None, None, None, None
+                    g, gd = ctx.saved_tensors
+                    gdd = (gF.to(gd.dtype) * gd).to(ctx.d_dtype) if ctx.needs_input_grad[1] else None
+                    return gF * g, gdd, None, None, None, None
 
             cls._fn = _F
-        return cls._fn.apply(theta, engine, inst, tau, precision)
+        if d is None:
+            d = torch.tensor(engine.ds[inst], dtype=torch.float64, device=theta.device)
+        return cls._fn.apply(theta, d, engine, inst, tau, precision)
 
 
 def class_representatives(engine) -> np.ndarray:
@@ -57,10 +68,10 @@ def class_representatives(engine) -> np.ndarray:
     return reps
 
 
-def theta_from_q(engine, q_host: np.ndarray, floor: float = 1e-300) -> np.ndarray:
-    """Logits whose softmax over classes is q (q orbit-invariant, by code)."""
-    reps = class_representatives(engine)
-    return np.log(np.maximum(q_host[reps], floor))
+def theta_from_q(engine, q, floor: float = 1e-300) -> np.ndarray:
+    """Logits whose softmax over classes is q (q orbit-invariant, by code),
+    computed by the library (bdc_class_logits)."""
+    return engine.class_logits(q, "fp64", floor).cpu().numpy()
 
 
 def optimize_dual(engine, inst: int = 0, tau: float = 1e-3, steps: int = 200, lr: float = 1e-2,

@@ -82,3 +82,42 @@ def test_autograd_and_direct_optimisation_tightens_bound():
     lo = oracle.ba_bdc(n, d, 1, p0=None)["lower"][0] if n <= 12 else 0.0
     assert res["certified_final"] >= lo
     eng.close()
+
+
+@pytest.mark.parametrize("n,d,tau", [(8, 0.7, 0.05), (9, 0.45, 0.02)])
+def test_autograd_d_gradient_matches_oracle(n, d, tau):
+    # d enters the autograd Function as a 0-d tensor: backward gives dF/dd
+    # (theta fixed) beside dF/dtheta, both against the oracle's gradient
+    bdc = _bdc()
+    from paper_2604_05867_b300 import dual
+    eng = bdc.Engine(n, [d], options=bdc.default_options(enable_literal=0))
+    ocls, _, _ = oracle.output_classes(n)
+    rng = np.random.default_rng(7 + n)
+    theta = rng.normal(scale=0.5, size=eng.num_output_classes)
+    F_ref, g_ref, gd_ref = oracle.dual_bound(n, d, tau, theta, ocls)
+    th = torch.tensor(theta, dtype=torch.float64, device="cuda", requires_grad=True)
+    dt = torch.tensor(d, dtype=torch.float64, device="cuda", requires_grad=True)
+    F = dual.DualBound.apply(th, eng, 0, tau, "fp64", d=dt)
+    (2.0 * F).backward()
+    assert abs(F.item() - F_ref) <= 1e-10 * max(1.0, abs(F_ref))
+    assert abs(dt.grad.item() - 2.0 * gd_ref) <= 1e-9 * max(1.0, abs(gd_ref))
+    assert np.all(np.abs(th.grad.cpu().numpy() - 2.0 * g_ref) <= 1e-9 * np.maximum(1.0, np.abs(g_ref)))
+    with pytest.raises(ValueError):
+        dual.DualBound.apply(th, eng, 0, tau, "fp64", d=torch.tensor(d + 0.1, dtype=torch.float64, device="cuda"))
+    eng.close()
+
+
+def test_class_logits_invert_the_softmax():
+    bdc = _bdc()
+    from paper_2604_05867_b300 import dual
+    n, d = 10, 0.6
+    eng = bdc.Engine(n, [d], options=bdc.default_options(enable_literal=0))
+    eng.iterate(5, -1.0, "fp64", "sweep")
+    q = eng.get_q("fp64")[0]
+    theta = dual.theta_from_q(eng, q)
+    cls = eng.output_classes()
+    # the logits are ln q at each class's codes
+    assert np.allclose(theta[cls[1:]], np.log(q[1:]), rtol=0, atol=1e-12)
+    q2 = eng.softmax_classes(0, torch.tensor(theta, dtype=torch.float64, device="cuda")).cpu().numpy()
+    assert np.all(np.abs(q2[1:] - q[1:]) <= 1e-12 * q[1:])
+    eng.close()

@@ -4,15 +4,18 @@ Some callers cannot allocate device memory (inside another component's CUDA
 graph capture, under a host framework that owns every allocation, or under
 strict memory accounting).  This entry point keeps its scratch in a fixed
 array inside the library instead.  Here it is called through the C ABI and
-compared with the engine's output marginal (bdc_get_q), to the 1e-12
-relative tolerance of the other FP64 marginal tests, on two calls in a row;
-calls of different sizes share the same scratch; sizes beyond the fixed
-array are rejected with a clear error."""
+compared with the oracle's q(y) = sum_x p(x) W(y|x) (Sec. 2.3, by its
+definition) to the 1e-12 relative tolerance of the other FP64 marginal
+tests, on two calls in a row, for orbit-invariant and for asymmetric p; it
+also agrees with the engine's own marginal (bdc_get_q); calls of different
+sizes share the same scratch; sizes beyond the fixed array are rejected with
+a clear error."""
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_2604_05867_b300 import inputs
 
 torch = pytest.importorskip("torch")
@@ -45,27 +48,41 @@ def _static_q(bdc, f, n, d, p):
     return q_dev.cpu().numpy()
 
 
-@pytest.mark.parametrize("n,d", [(16, 0.7), (11, 0.35)])
-def test_static_marginal_matches_engine_on_two_calls(n, d):
+def _close(q, q_ref):
+    nz = q_ref > 0
+    return q[0] == 0.0 and np.all(np.abs(q[nz] - q_ref[nz]) <= 1e-12 * q_ref[nz]) and np.all(q[~nz] == 0)
+
+
+@pytest.mark.parametrize("n,d,sym", [(16, 0.7, True), (11, 0.35, True), (14, 0.55, False)])
+def test_static_marginal_matches_oracle_on_two_calls(n, d, sym):
+    # n = 14 and 16 run the split (columns, rows, combine) schedule; the
+    # asymmetric p at n = 14 checks the full-mode kernels on inputs that are
+    # not complement- or reversal-invariant
     bdc, f = _fn()
-    p = inputs.orbit_invariant_dirichlet(n, seed=n)
-    q_ref = _engine_q(bdc, n, d, p)
+    if sym:
+        p = inputs.orbit_invariant_dirichlet(n, seed=n)
+    else:
+        p = np.random.default_rng(n).dirichlet(np.ones(1 << n))[None, :]
+    q_ref = oracle.q_full(n, d, p[0])
     for _ in range(2):
         q = _static_q(bdc, f, n, d, p)
-        assert q[0] == 0.0
-        assert np.all(np.abs(q[1:] - q_ref[1:]) <= 1e-12 * q_ref[1:])
+        assert _close(q, q_ref)
+    assert _close(_engine_q(bdc, n, d, p), q_ref)
 
 
 def test_static_marginal_shared_scratch_and_limit():
+    # n = 18 (the largest size the array holds) then n = 14 on the same
+    # scratch; n = 18 is checked against the oracle on sampled codes of every
+    # length, each summed over all 2^18 inputs from the definition
     bdc, f = _fn()
     pa = inputs.orbit_invariant_dirichlet(18, seed=1)
     pb = inputs.orbit_invariant_dirichlet(14, seed=2)
-    qa_ref = _engine_q(bdc, 18, 0.5, pa)
-    qb_ref = _engine_q(bdc, 14, 0.9, pb)
     qa = _static_q(bdc, f, 18, 0.5, pa)
     qb = _static_q(bdc, f, 14, 0.9, pb)
-    assert np.all(np.abs(qa[1:] - qa_ref[1:]) <= 1e-12 * qa_ref[1:])
-    assert np.all(np.abs(qb[1:] - qb_ref[1:]) <= 1e-12 * qb_ref[1:])
+    for c in inputs.random_codes(18, 10, seed=4):
+        r = oracle.q_point(18, 0.5, pa[0], int(c))
+        assert abs(qa[c] - r) <= 1e-12 * r
+    assert _close(qb, oracle.q_full(14, 0.9, pb[0]))
     dummy = torch.zeros(8, dtype=torch.float64, device="cuda")
     st = f(19, 0.5, ctypes.c_void_p(dummy.data_ptr()), ctypes.c_void_p(dummy.data_ptr()), None)
     assert st == -1 and b"18" in bdc.lib().bdc_last_error()
