@@ -98,6 +98,13 @@ typedef struct {
      * the per-thread 16-byte loads fill the tile faster (n = 24: 0.124 ms per
      * launch against 0.147 ms with TMA). */
     int use_tma;
+    /* Polls of that kernel's wait for its TMA tile before it gives up, sets
+     * BDC_ETIMEOUT for the instance, waits (bounded) for its copies still in
+     * flight and returns.  0: the default, 2^22 polls (about a second); a
+     * negative value: no poll at all, so the wait gives up at once (for
+     * tests of the timeout path).  The wait for the copies in flight always
+     * uses the default bound. */
+    int tma_wait_polls;
 } bdc_options;
 
 /* Fill *opt with the defaults above. */
@@ -193,7 +200,9 @@ bdc_status bdc_divergence(bdc_engine *eng, const void *q_dev, int precision, dou
  * array [nd][2^(n+1)] of doubles (positive at every code).  Host arrays of
  * nd: upper (the certified bound, rounded up), margin (the added rounding
  * margin, bits), lower (FP64 Blahut lower bound of the current p; NaN when
- * q_dev is given).  Any may be NULL. */
+ * q_dev is given).  Any may be NULL.  Errors: BDC_ENONFINITE (a NaN or Inf
+ * in the given q, or a non-finite bound), BDC_EINVAL (a given q that is not
+ * positive at every code); the values of the other instances are valid. */
 bdc_status bdc_certify_upper(bdc_engine *eng, const double *q_dev, double *upper, double *margin, double *lower);
 
 /* --- state access (caller-owned host buffers, copied) -------------------- */

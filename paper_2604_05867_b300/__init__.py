@@ -43,7 +43,7 @@ class Options(ctypes.Structure):
                 ("sched_n2_fp64", ctypes.c_int), ("sched_w_fp64", ctypes.c_int),
                 ("enable_literal", ctypes.c_int), ("use_half", ctypes.c_int),
                 ("use_regsteps", ctypes.c_int), ("fuse_update", ctypes.c_int),
-                ("use_tma", ctypes.c_int)]
+                ("use_tma", ctypes.c_int), ("tma_wait_polls", ctypes.c_int)]
 
 
 _lib = None

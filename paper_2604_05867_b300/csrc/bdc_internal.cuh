@@ -309,6 +309,12 @@ __device__ __forceinline__ void finalize_instance(int z, const double *part, int
     double ZD = fin_sum<NT>(p1, 4, nblk1, red);
     double mD = fin_max<NT>(p1 + 1, 4, nblk1, red);
     if (threadIdx.x != 0) return;
+    if (I[I_STATUS] != 0.0) {
+        // a kernel of this iteration failed (e.g. a bounded wait gave up): the
+        // instance stops and keeps that status
+        I[I_ACTIVE] = 0.0;
+        return;
+    }
     if (!isfinite(ZD) || !isfinite(mD) || !(Zp > 0.0) || !isfinite(Zp) || !(ZD > 0.0)) {
         I[I_STATUS] = (double)BDC_ENONFINITE;
         I[I_ACTIVE] = 0.0;

@@ -112,6 +112,26 @@ __global__ void k_log2_codes_nd(const T *q, T *L, size_t per, int nd, int min1) 
     }
 }
 
+// a caller-given output distribution must be finite and positive at every
+// code: record BDC_ENONFINITE (NaN or Inf) or BDC_EINVAL (<= 0) per instance
+__global__ void k_check_given_q(const double *q, size_t M, double *inst) {
+    const int z = blockIdx.y;
+    const double *qz = q + z * M;
+    int bad = 0;
+    for (size_t c = 1 + (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < M; c += (size_t)gridDim.x * blockDim.x) {
+        const double v = qz[c];
+        if (!isfinite(v)) bad |= 2;
+        else if (!(v > 0.0)) bad |= 1;
+    }
+    bad = __reduce_or_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0 && bad) {
+        double *st = inst + z * INST_STRIDE + I_STATUS;
+        // (where both kinds occur, either status may be the one recorded)
+        if (bad & 2) *st = (double)BDC_ENONFINITE;
+        else if (*st == 0.0) *st = (double)BDC_EINVAL;
+    }
+}
+
 // certified upper bound: U = max_x up(D'_x + m_x) + up(log2 sum q~ + e_Lambda)
 __global__ void k_finalize_cert(int nd, const double *part, int maxblk, int nb0, int nb1, double Kterms,
                                 int have_lower, double *inst) {
@@ -142,7 +162,7 @@ __global__ void k_finalize_cert(int nd, const double *part, int maxblk, int nb0,
     I[I_LOG2SQ] = Lam;
     I[I_LOG2SQ_ERR] = eL;
     I[I_CERT_LO] = have_lower ? (log2(S1 / Sp) + Lam) : NAN;
-    if (!isfinite(U)) I[I_STATUS] = (double)BDC_ENONFINITE;
+    if (!isfinite(U) && I[I_STATUS] == 0.0) I[I_STATUS] = (double)BDC_ENONFINITE;
 }
 
 int grid_for(size_t n, int threads, int cap = 148 * 32) {
@@ -717,7 +737,8 @@ extern "C" bdc_status bdc_ba_iterate(bdc_engine *e, int max_iters, double tol, i
         if (I[I_STATUS] != 0.0) st = (bdc_status)(int)I[I_STATUS];
     }
     e->iters_total += done;
-    if (st != BDC_OK) bdc_set_error("bdc_ba_iterate: non-finite value in a reduction");
+    if (st == BDC_ETIMEOUT) bdc_set_error("bdc_ba_iterate: a bounded device wait gave up (instance stopped)");
+    else if (st != BDC_OK) bdc_set_error("bdc_ba_iterate: non-finite value in a reduction (instance stopped)");
     return st;
 }
 
@@ -858,9 +879,10 @@ extern "C" bdc_status bdc_batch_iterate(bdc_batch *b, int max_iters, double tol,
     for (bdc_engine *e : b->engs) {
         BDC_TRY(read_inst(e, h));
         for (int z = 0; z < e->nd; z++)
-            if (h[(size_t)z * INST_STRIDE + I_STATUS] != 0.0) st = BDC_ENONFINITE;
+            if (h[(size_t)z * INST_STRIDE + I_STATUS] != 0.0) st = (bdc_status)(int)h[(size_t)z * INST_STRIDE + I_STATUS];
     }
-    if (st != BDC_OK) bdc_set_error("bdc_batch_iterate: non-finite value in a reduction");
+    if (st == BDC_ETIMEOUT) bdc_set_error("bdc_batch_iterate: a bounded device wait gave up (instance stopped)");
+    else if (st != BDC_OK) bdc_set_error("bdc_batch_iterate: non-finite value in a reduction (instance stopped)");
     return st;
 }
 
@@ -958,6 +980,7 @@ extern "C" bdc_status bdc_certify_upper(bdc_engine *e, const double *q_dev, doub
         k_sum_rows<double><<<dim3(g0, nd), 256, 0, e->stream>>>(b.q, M, b.part, maxblk, 2, e->bk, n); e->launches++;
         Lsrc = b.L;
     } else {
+        k_check_given_q<<<dim3(grid_for(M, 256, 1024), nd), 256, 0, e->stream>>>(q_dev, M, e->inst); e->launches++;
         k_log2_codes_nd<double><<<grid_for(nd * M, 256), 256, 0, e->stream>>>(q_dev, b.aux, M, nd, 1); e->launches++;
         k_sum_rows<double><<<dim3(g0, nd), 256, 0, e->stream>>>(q_dev, M, b.part, maxblk, 2, nullptr, n); e->launches++;
         Lsrc = b.aux;
@@ -975,9 +998,10 @@ extern "C" bdc_status bdc_certify_upper(bdc_engine *e, const double *q_dev, doub
         if (upper) upper[z] = I[I_CERT_U];
         if (margin) margin[z] = I[I_CERT_M];
         if (lower) lower[z] = I[I_CERT_LO];
-        if (I[I_STATUS] != 0.0) st = BDC_ENONFINITE;
+        if (I[I_STATUS] != 0.0 && st != BDC_ENONFINITE) st = (bdc_status)(int)I[I_STATUS];
     }
-    if (st != BDC_OK) bdc_set_error("bdc_certify_upper: non-finite certified value");
+    if (st == BDC_EINVAL) bdc_set_error("bdc_certify_upper: the given q must be positive at every code");
+    else if (st != BDC_OK) bdc_set_error("bdc_certify_upper: non-finite value (in the given q or the certified bound)");
     return st;
 }
 

@@ -720,9 +720,10 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tm, in
         "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(smem_u32(m))
         : "memory");
 }
-// bounded wait for phase `parity` (about a second at most); false: gave up
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *m, uint32_t parity) {
-    for (uint32_t it = 0; it < (1u << 22); it++)
+// bounded wait for phase `parity`: at most `polls` polls (2^22, the
+// default, is about a second); false: gave up
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *m, uint32_t parity, uint32_t polls = (1u << 22)) {
+    for (uint32_t it = 0; it < polls; it++)
         if (mbar_try_wait(m, parity)) return true;
     return false;
 }
@@ -742,6 +743,7 @@ struct SweepArgs {
     // column step kernel: load the Gb tile with TMA through the kernel's
     // tensor map (complement half mode, 4 columns, n1 >= 9; see k_cols_adj_l)
     int tma;
+    uint32_t tma_polls;       // polls of the TMA tile wait before BDC_ETIMEOUT
 };
 
 // rows of the Gb tile that the TMA form loads, in 256-row boxes: slots 0, 1
@@ -1501,7 +1503,7 @@ k_cols_adj_l(SweepArgs a, EpiArgs ep, const T *__restrict__ Gb, T *__restrict__ 
                     tma_load_2d(stage + ((sl * 256u) << 2), &tmG, xm, y0 + (int)row0, &mbar);
                 }
             }
-            const bool ok = mbar_wait_bounded(&mbar, 0);
+            const bool ok = mbar_wait_bounded(&mbar, 0, a.tma_polls);
             if (__syncthreads_or(!ok)) {
                 // a copy did not arrive in time: report, wait (bounded) for the
                 // copies still in flight into this CTA's shared memory, return
@@ -1790,6 +1792,8 @@ SweepArgs make_args(bdc_engine *e, PrecBuf<T> &b) {
     a.q_floor = e->opt.q_floor;
     a.inv_binom = e->bk + (size_t)4 * e->nd * (e->n + 1);
     a.q_floor_f = (float)e->opt.q_floor;
+    a.tma_polls = e->opt.tma_wait_polls == 0 ? (1u << 22)
+                                             : (e->opt.tma_wait_polls < 0 ? 0u : (uint32_t)e->opt.tma_wait_polls);
     double c = 1.0;  // C(n,k), exact in double for n <= 26
     for (int k = 0; k <= e->n; k++) {
         a.inv_binom_f[k] = (float)(1.0 / c);
