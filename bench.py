@@ -70,27 +70,36 @@ def stage_bytes(n: int, n1: int, n2: int, elem: int, half: bool) -> dict:
     }
 
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of each
-# FP32 iteration kernel, from one ncu capture of this bench's own workload
-# (profiles/<kernel>_n24.md), keyed by stage, n and the (n1, n2, width)
-# schedule.  A kernel changed since its capture must be removed from here.
-MEASURED_TRAFFIC = {
-    ("cols_step", 24, 11, 13, 4): 134.635008e6 + 30.761472e6,
-    ("cols_step", 24, 11, 13, 8): 134.29888e6 + 36.823808e6,
-    ("rows_adj", 24, 11, 13, 4): 75.447552e6 + 34.15168e6,
-    ("combine", 24, 11, 13, 4): 134.210304e6 + 28.534528e6,
-    ("rows_fwd", 24, 11, 13, 4): 67.13984e6 + 20.333312e6,
-}
+# ncu counters of the FP32 iteration kernels (DRAM bytes read + written and
+# shared-memory wavefronts per launch), one capture of this bench's own
+# workload, summarised in a JSON file beside the text summaries of the same
+# captures.  The file records a hash of the kernel source it was taken from;
+# once that source changes the counters no longer describe the kernels and
+# are reported as null.
+COUNTERS = os.path.join(ROOT, "profiles", "ncu_counters_n24.json")
+KERNEL_SOURCE = os.path.join(ROOT, "paper_2604_05867_b300", "csrc", "sweep.cu")
 
-# Shared-memory wavefronts (128 B each) per launch of the same kernels, from
-# the same captures (l1tex__data_pipe_lsu_wavefronts_mem_shared.sum): the
-# shared-memory sweep kernels are bound by shared memory, not by DRAM.
-MEASURED_SMEM_WAVEFRONTS = {
-    ("cols_step", 24, 11, 13, 4): 14724270,
-    ("cols_step", 24, 11, 13, 8): 14905774,
-    ("rows_adj", 24, 11, 13, 4): 18092612,
-    ("rows_fwd", 24, 11, 13, 4): 14390558,
-}
+
+def kernel_source_hash() -> str:
+    import hashlib
+    with open(KERNEL_SOURCE, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def measured_counters(stage: str, n: int, sched: dict):
+    """(dram_bytes, smem_wavefronts, source) of one launch of `stage`, or
+    (None, None, why) when no capture of the current kernels exists."""
+    try:
+        with open(COUNTERS) as f:
+            j = json.load(f)
+    except Exception:
+        return None, None, "no counter file"
+    if j.get("source_sha") != kernel_source_hash():
+        return None, None, "kernels changed since the capture"
+    for r in j.get("launches", []):
+        if (r["stage"], r["n"], r["n1"], r["n2"], r["width"]) == (stage, n, sched["n1"], sched["n2"], sched["width"]):
+            return r.get("dram_bytes"), r.get("smem_wavefronts"), j.get("command", "")
+    return None, None, "no capture of this schedule"
 
 
 # ----------------------------------------------------------------------------
@@ -160,15 +169,19 @@ def measured_peaks() -> dict:
 # ----------------------------------------------------------------------------
 # oracle timing (host cores) -- the CPU baseline and the reference arm
 # ----------------------------------------------------------------------------
-def oracle_rate(n: int, d: float, seconds: float, seed: int = 0):
-    """Time the FP64 oracle's divergence walk on random inputs of length n
-    until about `seconds` of work; returns (pair-evals/s for a full iteration,
-    cores, sample description).  A BA iteration of the oracle walks every
-    (x, distinct y) pair twice (output marginal, then divergence) at the same
-    cost per pair, so the full-iteration rate is half the walk rate."""
+def oracle_rate(n: int, d: float, seconds: float, seed: int = 0, threads: int = 0):
+    """Time the FP64 oracle's divergence walk (the definition: every (x,
+    distinct y) pair) on random inputs of length n until about `seconds` of
+    work; returns (pair-evals/s for a full iteration, threads, sample
+    description, seconds).  A BA iteration of the oracle walks every pair
+    twice (output marginal, then divergence) at the same cost per pair, so
+    the full-iteration rate is half the walk rate.  The pairs are counted
+    outside the timed calls."""
     import oracle
     from paper_2604_05867_b300 import inputs
 
+    used = oracle.set_threads(threads if threads > 0 else (len(os.sched_getaffinity(0))
+                                                            if hasattr(os, "sched_getaffinity") else os.cpu_count()))
     q = np.ones(2 << n)  # any positive q: the walk's cost does not depend on its values
     q[0] = 0.0
     size, total_pairs, total_t, total_x = 32, 0, 0.0, 0
@@ -178,18 +191,34 @@ def oracle_rate(n: int, d: float, seconds: float, seed: int = 0):
         t0 = time.perf_counter()
         oracle.D_list(n, d, q, xs)
         dt = time.perf_counter() - t0
-        total_pairs += oracle.pairs_list(n, xs)  # counted outside the timed call
+        total_pairs += oracle.pairs_list(n, xs)
         total_t += dt
         total_x += size
         it += 1
         if dt < seconds / 8:
             size *= 2
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     rate = total_pairs / total_t / 2.0
-    sample = ("divergence walk of the FP64 oracle (OpenMP) over %d random inputs of length %d, %d pairs in %.1f s; "
-              "full-iteration rate = half the walk rate (marginal + divergence passes)" % (total_x, n, total_pairs,
-                                                                                           total_t))
-    return rate, cores, sample, total_t
+    sample = ("divergence walk of the FP64 oracle on %d thread(s) over %d random inputs of length %d, %d pairs in "
+              "%.1f s, extrapolated to a full iteration (2 (2*3^n - 2^n) pairs: marginal + divergence passes)"
+              % (used, total_x, n, total_pairs, total_t))
+    return rate, used, sample, total_t
+
+
+def oracle_sweep_rate(n: int, d: float, iters: int = 1):
+    """The oracle's factorised sweep (O2, same algorithm as the GPU path, plain
+    FP64 C with OpenMP) timed over `iters` full BA iterations at length n on
+    all host cores: output marginal, log2, transposed sweep, D, bounds, update.
+    The d-free entropy table S it reads is zero-filled here (its values do not
+    change the time; computing it is the once-per-n precompute, timed apart on
+    the GPU).  Returns (effective pair-evals/s, ms per iteration, threads)."""
+    import oracle
+    used = oracle.set_threads(len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count())
+    S = np.zeros((1 << n, n + 1))
+    p = np.full(1 << n, 1.0 / (1 << n))
+    t0 = time.perf_counter()
+    oracle.ba_sweep(n, d, iters, p0=p, S=S)
+    dt = (time.perf_counter() - t0) / iters
+    return pairs_per_iteration(n) / dt, 1000.0 * dt, used
 
 
 def run_reference(args, rank: int, world: int):
@@ -211,7 +240,9 @@ def run_reference(args, rank: int, world: int):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "BA iteration on BDC_d, n=24, d=0.5 (all 2^24 inputs)", "n": n, "d": [D_VALUE],
+        "config": {"workload": "BA iteration on BDC_d, n=24, d=0.5 (all 2^24 inputs); each step times the FP64 "
+                               "oracle's divergence walk on a random sample of inputs and extrapolates it to the "
+                               "full iteration", "n": n, "d": [D_VALUE], "extrapolated": True,
                    "parallelism": "host cores (OpenMP)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": "per step: " + sample},
@@ -291,24 +322,23 @@ def run_ours(args, rank: int, world: int):
             half = sched32["n2"] > 0 and sched32["width"] < (1 << sched32["n2"])
             sb = stage_bytes(n, sched32["n1"], sched32["n2"], 4, half)
             peaks = measured_peaks()
+            dev_peaks = bdc.measure_peaks(stream)
             top = max((k for k in stages if k in sb and sb[k] > 0), key=lambda k: stages[k])
             achieved = sb[top] / (stages[top] / 1000.0) / 1e9
-            traffic = MEASURED_TRAFFIC.get((top, n, sched32["n1"], sched32["n2"], sched32["width"]))
+            dram, wf, csrc = measured_counters(top, n, sched32)
             roof = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                    "frac": achieved / peaks["hbm_gbs"], "traffic": dram,
                     "peak_source": peaks["source"], "algorithmic_bytes": sb[top],
-                    "note": "complement half mode: %s" % half}
-            wf = MEASURED_SMEM_WAVEFRONTS.get((top, n, sched32["n1"], sched32["n2"], sched32["width"]))
+                    "traffic_source": csrc, "note": "complement half mode: %s" % half}
             if wf is not None:
-                # the kernel's binding resource: shared-memory bandwidth, 128 B
-                # per SM per clock at the maximum SM clock
-                props = torch.cuda.get_device_properties(dev)
-                smem_peak = props.multi_processor_count * 128 * (clk.get("sm_max_mhz") or 2032.0) * 1e6 / 1e12
+                # the kernel's binding on-chip resource: shared-memory bandwidth,
+                # against the peak measured in this run (bdc_measure_peaks)
                 smem_tb = wf * 128 / (stages[top] / 1000.0) / 1e12
-                roof["shared_memory"] = {"bytes_per_launch": wf * 128, "achieved": smem_tb, "peak": smem_peak,
-                                         "unit": "TB/s", "frac": smem_tb / smem_peak,
-                                         "source": "ncu shared-memory wavefronts of one launch x 128 B / "
-                                                   "this run's event time; peak = SMs x 128 B/clk x max SM clock"}
+                roof["shared_memory"] = {"bytes_per_launch": wf * 128, "achieved": smem_tb,
+                                         "peak": dev_peaks["smem_tbs"], "unit": "TB/s",
+                                         "frac": smem_tb / dev_peaks["smem_tbs"],
+                                         "source": "ncu shared-memory wavefronts of one launch x 128 B / this run's "
+                                                   "event time; peak measured in this run"}
             stage_total = sum(stages.values())
 
             # FP64 sweep iteration (same-algorithm precision baseline)
@@ -321,6 +351,14 @@ def run_ours(args, rank: int, world: int):
             e1.record(stream)
             torch.cuda.synchronize()
             ms64 = e0.elapsed_time(e1) / 5
+            # its additions against the FP64 pipe measured in this run: one
+            # forward step adds two terms and one adjoint step one, per element,
+            # over the columns (2^(n1+1) x 2^n2 elements, n1 steps) and rows
+            # (2^(n1+1) x 2^(n2+1), n2 steps) passes; halved in half mode
+            half64 = sched64["n2"] > 0 and sched64["width"] < (1 << sched64["n2"])
+            el_steps = (2 << n) * sched64["n1"] + (4 << n) * sched64["n2"]
+            adds64 = 3 * el_steps // (2 if half64 else 1)
+            fp64_rate = adds64 / (ms64 / 1000.0) / 1e12
 
             # FP64 certificate of the current p
             e0.record(stream)
@@ -358,19 +396,25 @@ def run_ours(args, rank: int, world: int):
                 del beng
                 torch.cuda.empty_cache()
 
-            # end to end through the public API: one Engine.iterate(1) call per
-            # step, bounds read back to the host every step
-            K = max(10, min(args.steps, 50))
-            # (setup, as for the timed region above: the replayed graphs are built
-            # and three untimed calls run first)
-            eng.prepare("fp32", "sweep")
-            for _ in range(3):
-                eng.iterate(1, -1.0, "fp32", "sweep")
+            # end to end through the public API, as a user job: the input
+            # distribution comes from pinned host memory (bdc_set_p: host->device
+            # copy and the device checks), K FP32 BA iterations (bdc_ba_iterate),
+            # the per-iteration bounds back to the host (bdc_get_history) and the
+            # FP64 certificate of the result (bdc_certify_upper, host outputs);
+            # per step = the job's wall time / K, bytes per step likewise
+            K = args.steps
+            p0 = torch.full((1, 1 << n), 1.0 / (1 << n), dtype=torch.float64).pin_memory().numpy()
+            eng.set_p(p0)
+            eng.prepare("fp32", "sweep")  # (setup: the replayed graphs exist before the job)
+            eng.iterate(K, -1.0, "fp32", "sweep")
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            for _ in range(K):
-                eng.iterate(1, -1.0, "fp32", "sweep")
+            eng.set_p(p0)
+            eng.iterate(K, -1.0, "fp32", "sweep")
+            hist = eng.history(0, K)
+            cert_e2e = eng.certify()
             e2e_s = (time.perf_counter() - t0) / K
+            assert len(hist[0]) == K and np.isfinite(cert_e2e["upper"][0])
             extra = {
                 "roofline": roof,
                 "stages_ms": stages,
@@ -383,6 +427,8 @@ def run_ours(args, rank: int, world: int):
                     "precompute_a0_s": a0_s,
                     "batched_4d_ms_per_iter_all": ms_batch,
                     "batched_4d_pair_evals_per_s": (4 * pairs_per_iteration(n) / (ms_batch / 1000.0)) if ms_batch else None,
+                    "fp64_sweep_adds_per_s_1e12": fp64_rate,
+                    "fp64_sweep_frac_of_measured_fp64_pipe": fp64_rate / dev_peaks["fp64_tops"],
                     "speedup_fp32_vs_fp64_sweep": ms64 / ms,
                     "speedup_fp32_sweep_vs_fp64_literal": (ms_lit / ms) if ms_lit else None,
                     "speedup_fp64_sweep_vs_fp64_literal": (ms_lit / ms64) if ms_lit else None,
@@ -390,14 +436,27 @@ def run_ours(args, rank: int, world: int):
                     "certify_margin_bits": float(cert["margin"][0]),
                     "lower_after_run": float(lo[0]), "upper_after_run": float(up[0]),
                 },
-                "e2e": {"value": pairs_per_iteration(n) / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
-                        "d2h_bytes_per_step": 32 * 8, "ms_per_step": e2e_s * 1000.0,
-                        "call": "Engine.iterate(1) -> bdc_ba_iterate, bounds read back each step"},
+                "e2e": {"value": pairs_per_iteration(n) / e2e_s, "unit": UNIT,
+                        "h2d_bytes_per_step": (8 << n) / K, "d2h_bytes_per_step": 16.0 + 24.0 / K,
+                        "ms_per_step": e2e_s * 1000.0, "steps": K,
+                        "call": "one job per K steps: Engine.set_p(pinned host p0) -> bdc_set_p; "
+                                "Engine.iterate(K) -> bdc_ba_iterate; Engine.history -> bdc_get_history; "
+                                "Engine.certify -> bdc_certify_upper; wall time / K"},
+                "device_peaks": dict(dev_peaks, source="bdc_measure_peaks in this run"),
             }
             if world == 1 and not args.skip_cpu:
                 rate, cores, sample, _ = oracle_rate(n, d, args.cpu_seconds)
                 extra["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                          "sample": sample}
+                r1, _, sample1, _ = oracle_rate(n, d, args.cpu_seconds / 3, threads=1)
+                extra["cpu_baseline_single_thread"] = {"value": r1, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                                       "sample": sample1}
+                r2, ms2, c2 = oracle_sweep_rate(n, d, 1)
+                extra["cpu_baseline_same_algorithm"] = {
+                    "value": r2, "unit": UNIT, "cores": c2, "kind": "oracle (factorised sweep, O2)",
+                    "ms_per_iteration": ms2,
+                    "sample": "one full FP64 BA iteration at n=%d on the oracle's factorised sweep; effective "
+                              "pair-evals/s = (2*3^n - 2^n) / its time" % n}
         eng.close()
 
     if rank == 0:
@@ -433,13 +492,20 @@ def run_config(args):
     import torch
 
     import paper_2604_05867_b300 as bdc
-    from paper_2604_05867_b300 import dual, inputs
+    from paper_2604_05867_b300 import dual, inputs, shard
 
-    torch.cuda.set_device(0)
+    # under torchrun the instance grids of the batched and large configurations
+    # are split over the ranks (one GPU each; instances are independent, so no
+    # data-path collective), results gathered on rank 0, time = max over ranks
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    rank, world = shard.init_from_env("nccl")
     stream = torch.cuda.Stream()
-    res = {"config_run": args.config}
+    res = {"config_run": args.config, "ranks": world}
     with torch.cuda.stream(stream):
-        if args.config == "ba10":
+        if rank != 0 and args.config not in ("batched", "large"):
+            pass  # single-GPU configurations run on rank 0 alone
+        elif args.config == "ba10":
             # plain FP64 BA at n=10, d=0.5: gap < 1e-9 or 2000 iterations; against the
             # oracle's BA on the channel built from all 2^10 deletion patterns
             import oracle
@@ -485,8 +551,8 @@ def run_config(args):
                 res["oracle_certify"] = {"U": U, "diff": float(c["upper"][0]) - U, "seconds": time.perf_counter() - t0}
             eng.close()
         elif args.config == "batched":
-            # n=22 with 32 d in [0.05, 0.95] and n in {14,16,18,20} with 8 d each, one graph
-            grid = inputs.batched_d_grid()
+            # n=22 with 32 d in [0.05, 0.95] and n in {14,16,18,20} with 8 d each, one graph per rank
+            grid = shard.shard_grid(inputs.batched_d_grid(), rank, world)
             T = args.iters or 500
             opts = bdc.default_options(enable_literal=0, chunk=10)
             engs = [bdc.Engine(n, ds, options=opts, stream=stream) for n, ds in grid.items()]
@@ -494,15 +560,28 @@ def run_config(args):
                 e.autotune("fp32")
             batch = bdc.Batch(engs, chunk=10)
             batch.iterate(10, -1.0, "fp32")
+            torch.cuda.synchronize()
+            if world > 1:
+                torch.distributed.barrier()
             ran, t = _sync_time(lambda: batch.iterate(T, -1.0, "fp32"), stream)
+            t = shard.max_over_ranks(t, device=torch.device("cuda", local))
             pairs = sum(pairs_per_iteration(e.n) * e.nd for e in engs)
             certs, tc = _sync_time(lambda: [e.certify() for e in engs], stream)
-            res.update({"instances": sum(e.nd for e in engs), "iters": ran, "seconds": t,
-                        "ms_per_iter_all_instances": 1000 * t / ran,
-                        "pairs_per_s_effective": pairs * ran / t, "certify_seconds_all": tc,
-                        "certified_upper_over_n": {str(e.n): [round(float(u) / e.n, 8) for u in c["upper"]]
-                                                   for e, c in zip(engs, certs)},
-                        "max_margin": max(float(np.max(c["margin"])) for c in certs)})
+            mine = {"pairs": pairs, "instances": sum(e.nd for e in engs), "iters": ran,
+                    "certified_upper_over_n": {str(e.n): [round(float(u) / e.n, 8) for u in c["upper"]]
+                                               for e, c in zip(engs, certs)},
+                    "d": {str(e.n): e.ds for e in engs},
+                    "max_margin": max(float(np.max(c["margin"])) for c in certs), "certify_seconds": tc}
+            parts = shard.gather_to_rank0(mine)
+            if rank == 0:
+                tot_pairs = sum(m["pairs"] for m in parts)
+                res.update({"instances": sum(m["instances"] for m in parts), "iters": ran, "seconds": t,
+                            "ms_per_iter_all_instances": 1000 * t / ran,
+                            "pairs_per_s_effective": tot_pairs * ran / t,
+                            "certify_seconds_max_rank": max(m["certify_seconds"] for m in parts),
+                            "per_rank": [{"d": m["d"], "certified_upper_over_n": m["certified_upper_over_n"]}
+                                         for m in parts],
+                            "max_margin": max(m["max_margin"] for m in parts)})
             batch.close()
             for e in engs:
                 e.close()
@@ -562,26 +641,117 @@ def run_config(args):
         elif args.config == "large":
             # n=26, 7 values of d, 300 FP32 iterations each, FP64 certificate of C_26(d)/(26(1-d))
             from paper_2604_05867_b300.inputs import LARGE_SWEEP_D
-            n, T = 26, args.iters or 300
-            ds = LARGE_SWEEP_D
+            n, T = args.n or 26, args.iters or 300
+            ds = shard.shard_grid({n: list(LARGE_SWEEP_D)}, rank, world).get(n, [])
+            mine = {"d": ds}
+            if ds:
+                t0 = time.perf_counter()
+                eng = bdc.Engine(n, ds, options=bdc.default_options(enable_literal=0), stream=stream)
+                t_bind = time.perf_counter() - t0
+                eng.autotune("fp32")
+                torch.cuda.synchronize()
+            if world > 1:
+                torch.distributed.barrier()
+            if ds:
+                (lo, up, it), t = _sync_time(lambda: eng.iterate(T, -1.0, "fp32", "sweep"), stream)
+                c, tc = _sync_time(lambda: eng.certify(), stream)
+                mine.update({"bind_precompute_s": t_bind, "seconds": t, "certify_seconds": tc,
+                             "workspace_gb": eng.ws_bytes / 1e9,
+                             "certified_upper": [float(u) for u in c["upper"]],
+                             "certified_over_n_1_minus_d": [float(u) / (n * (1 - dv)) for u, dv in zip(c["upper"], ds)],
+                             "margin_max": float(np.max(c["margin"])),
+                             "lower_last": [float(v) for v in lo], "upper_last": [float(v) for v in up]})
+                eng.close()
+            else:
+                mine["seconds"] = 0.0
+            t = shard.max_over_ranks(mine["seconds"], device=torch.device("cuda", local))
+            parts = shard.gather_to_rank0(mine)
+            if rank == 0:
+                alld = [d_ for m in parts for d_ in m["d"]]
+                res.update({"n": n, "d": alld, "iters": T, "seconds": t, "ms_per_iter_all_instances": 1000 * t / T,
+                            "pairs_per_s_effective": pairs_per_iteration(n) * len(alld) * T / t,
+                            "per_rank": parts})
+        elif args.config == "literal":
+            # the plain FP64 GPU form on its own: literal enumeration iterations
+            # (supersequence walk for q, subsequence walk for D, on orbit
+            # representatives); a small case for profiling its kernels
+            n, d, T = args.n or 20, 0.5, args.iters or 2
+            eng = bdc.Engine(n, [d], options=bdc.default_options(enable_literal=1), stream=stream)
+            eng.iterate(1, -1.0, "fp64", "literal")
+            (lo, up, it), t = _sync_time(lambda: eng.iterate(T, -1.0, "fp64", "literal"), stream)
+            from math import comb
+            # leaves of the supersequence walk: every output class of length k
+            # has sum_{i <= n-k} C(n, i) supersequences (Lemma num_superseq)
+            rk = [1] + [((1 << k) + (1 << ((k + 1) // 2)) + ((1 << (k // 2)) if k % 2 == 0 else 0)) // 4
+                        for k in range(1, n + 1)]
+            q_leaves = sum(rk[k] * sum(comb(n, i) for i in range(n - k + 1)) for k in range(n + 1))
+            d_nodes = pairs_per_iteration(n) / 4.0  # distinct (rep x, y) pairs, orbit-reduced (up to fixed points)
+            res.update({"n": n, "d": d, "iters": T, "ms_per_iter": 1000 * t / T, "lower": float(lo[0]),
+                        "upper": float(up[0]), "q_walk_leaves_per_iter": q_leaves,
+                        "d_walk_pairs_per_iter_approx": d_nodes,
+                        "enumerated_pairs_per_s": (q_leaves + d_nodes) * T / t,
+                        "stages_ms": eng.profile("fp64", "literal", reps=1)})
+            eng.close()
+        elif args.config == "exact":
+            # exact deletion channels BDC_{n,k} for every k in one engine of
+            # length-mixture instances, certified; then C(d) bounds by Lemma
+            # prob-vs-exact on the grid of the paper's C(d) table, the
+            # high-noise constant by Lemma convex, and Lemma worse-UB (s = 2)
+            # from C_{n-2,k}
+            from paper_2604_05867_b300 import bounds
+            n, T, tol = args.n or 24, args.iters or 3000, 1e-4
             t0 = time.perf_counter()
-            eng = bdc.Engine(n, ds, options=bdc.default_options(enable_literal=0), stream=stream)
-            t_bind = time.perf_counter() - t0
-            eng.autotune("fp32")
-            (lo, up, it), t = _sync_time(lambda: eng.iterate(T, -1.0, "fp32", "sweep"), stream)
-            c, tc = _sync_time(lambda: eng.certify(), stream)
-            res.update({"n": n, "d": ds, "iters": T, "bind_precompute_s": t_bind, "seconds": t,
-                        "ms_per_iter_all_instances": 1000 * t / T,
-                        "pairs_per_s_effective": pairs_per_iteration(n) * len(ds) * T / t,
-                        "certify_seconds": tc, "workspace_gb": eng.ws_bytes / 1e9,
-                        "certified_upper": [float(u) for u in c["upper"]],
-                        "certified_over_n_1_minus_d": [float(u) / (n * (1 - dv)) for u, dv in zip(c["upper"], ds)],
-                        "margin_max": float(np.max(c["margin"])),
-                        "lower_last": [float(v) for v in lo], "upper_last": [float(v) for v in up]})
+            res_k = bounds.exact_capacities(n, list(range(0, n + 1)), iters=T, tol=tol, precision="fp32",
+                                            options=bdc.default_options(enable_literal=0), stream=stream)
+            t_exact = time.perf_counter() - t0
+            Cnk = [res_k[k]["upper"] for k in range(n + 1)]
+            grid = [0.01, 0.02, 0.03, 0.04, 0.05, 0.10, 0.15, 0.20, 0.25, 0.30, 0.35, 0.40, 0.45, 0.50, 0.55,
+                    0.60, 0.64, 0.65, 0.68]
+            cd = bounds.cd_table(grid, {n: Cnk})
+            _, ratio = bounds.high_noise(0.64, [v for d_, v, _ in cd if d_ == 0.64][0])
+            # Lemma worse-UB from the exact channels of length n - 2 (certified
+            # the same way) and C_{2,0..2} = 0, 1, 2
+            res_m = bounds.exact_capacities(n - 2, list(range(0, n - 1)), iters=T, tol=tol, precision="fp32",
+                                            options=bdc.default_options(enable_literal=0), stream=stream)
+            Cm = [res_m[k]["upper"] for k in range(n - 1)]
+            split = {k: bounds.split_bound(n, k, 2, [0.0, 1.0, 2.0], Cm) for k in range(n + 1)}
+            # the direct BDC_d engine at three d: the lemma's bound is never below
+            # its certified lower bound
+            direct = {}
+            for dv in (0.1, 0.5, 0.64):
+                e = bdc.Engine(n, [dv], options=bdc.default_options(enable_literal=0), stream=stream)
+                lo, up, it = e.iterate(T, tol, "fp32", "sweep")
+                c = e.certify()
+                direct[str(dv)] = {"certified_upper_over_n": float(c["upper"][0]) / n,
+                                   "lower_over_n": float(c["lower"][0]) / n, "iters": int(it[0]),
+                                   "prob_vs_exact_over_n": bounds.prob_vs_exact(n, dv, Cnk) / n}
+                e.close()
+            res.update({"n": n, "tol_bits": tol, "seconds_all_k": t_exact,
+                        "Cnk_certified": {str(k): res_k[k]["upper"] for k in res_k},
+                        "Cnk_iters": {str(k): res_k[k]["iters"] for k in res_k},
+                        "Cnk_gap": {str(k): res_k[k]["ba_upper"] - res_k[k]["ba_lower"] for k in res_k},
+                        "Cnk_table": bounds.ck_table(n, {k: res_k[k]["upper"] for k in range(1, n + 1)}),
+                        "worse_ub_from_n_minus_2": {str(k): v for k, v in split.items()},
+                        "Cd_table": [{"d": d_, "bound": bounds.ceil4(v), "n": nb} for d_, v, nb in cd],
+                        "high_noise_ratio_at_0.64": bounds.ceil4(ratio), "direct_bdc": direct})
+        elif args.config == "fp64sweep":
+            # FP64 sweep iterations at n = 24 (the same-algorithm precision
+            # baseline); a case for profiling the FP64 sweep kernels
+            n, d, T = args.n or 24, 0.5, args.iters or 5
+            eng = bdc.Engine(n, [d], options=bdc.default_options(enable_literal=0), stream=stream)
+            sched = eng.autotune("fp64", reps=2)
+            eng.iterate(2, -1.0, "fp64", "sweep")
+            (lo, up, it), t = _sync_time(lambda: eng.iterate(T, -1.0, "fp64", "sweep"), stream)
+            res.update({"n": n, "d": d, "iters": T, "ms_per_iter": 1000 * t / T, "schedule_fp64": sched,
+                        "stages_ms": eng.profile("fp64", "sweep", reps=2),
+                        "device_peaks": bdc.measure_peaks(stream)})
             eng.close()
         else:
             raise SystemExit("unknown config " + args.config)
-    print(json.dumps(res), flush=True)
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
 
 
 def main():
@@ -594,9 +764,11 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-literal", action="store_true")
     ap.add_argument("--skip-batched", action="store_true")
-    ap.add_argument("--config", default=None, choices=["ba10", "n20", "batched", "dual", "large"],
+    ap.add_argument("--config", default=None,
+                    choices=["ba10", "n20", "batched", "dual", "large", "literal", "fp64sweep", "exact"],
                     help="run one workload configuration end to end instead of the headline bench")
     ap.add_argument("--iters", type=int, default=0)
+    ap.add_argument("--n", type=int, default=0, help="input length of the literal / fp64sweep / exact configs")
     ap.add_argument("--sched-fp32", default=None, metavar="N2,W",
                     help="use this FP32 sweep schedule (n2, column width) instead of the autotuner's")
     ap.add_argument("--sched-cache", default=None,

@@ -61,8 +61,9 @@ typedef struct {
     /* Iterations per graph launch when use_graph (default 8).  The host reads
      * the per-instance stop flags after each launch. */
     int chunk;
-    /* Floor applied to the per-length output marginal before its log (FP32
-     * iterations only; keeps log2 finite if p underflowed).  Default 1e-30. */
+    /* Floor applied to the per-length output marginal before its log in BA
+     * iterations (both precisions; keeps log2 finite if p underflowed in
+     * FP32; 0 = no floor).  The certificate never floors.  Default 1e-30. */
     double q_floor;
     /* Weight of the uniform input mixed into p before certification, so the
      * certified output distribution is positive everywhere.  Default 2^-30. */
@@ -281,6 +282,16 @@ int64_t bdc_launch_count(const bdc_engine *eng);
  * they advance p like bdc_ba_iterate. */
 bdc_status bdc_profile_iteration(bdc_engine *eng, int precision, int impl, int reps, double *stage_ms, char *names,
                                  int names_len, int *nstages);
+
+/* Microbenchmarks of this device, run on cuda_stream and timed with CUDA
+ * events (the peaks the sweep and walk kernels are measured against):
+ * out[0] = FP32 FMA instructions per second / 1e12 (an add takes the same
+ * pipe slot), out[1] = the same in FP64, out[2] = L2 read bandwidth in GB/s
+ * (a 32 MiB buffer read over repeatedly), out[3] = shared-memory bandwidth
+ * in TB/s (16-byte accesses), out[4] = number of SMs.  scratch_dev: device
+ * buffer of at least 64 MiB, 16-byte aligned, caller-owned (overwritten).
+ * Synchronous.  Errors: BDC_EINVAL, BDC_ECUDA. */
+bdc_status bdc_measure_peaks(void *scratch_dev, size_t bytes, void *cuda_stream, double *out);
 
 /* Schedule of the sweep in `precision`: input split n1 + n2 (n2 = 0: one
  * pass) and the column tile width. */

@@ -91,6 +91,7 @@ def lib():
             "bdc_batch_iterate": (I, [P, I, D, I, P]),
             "bdc_batch_destroy": (None, [P]),
             "bdc_profile_iteration": (I, [P, I, I, I, P, ctypes.c_char_p, I, P]),
+            "bdc_measure_peaks": (I, [P, SZ, P, P]),
             "bdc_last_error": (ctypes.c_char_p, []),
         }
         for name, (res, args) in sig.items():
@@ -419,3 +420,15 @@ def subseq_counts(n: int, xs, emb: bool = False, stream=None):
                                    ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(E.data_ptr()) if emb else None,
                                    sh))
     return N, S, E
+
+
+def measure_peaks(stream=None) -> dict:
+    """Device microbenchmarks (bdc_measure_peaks): FP32 / FP64 FMA-or-add
+    instruction rates (1e12/s), L2 read GB/s, shared-memory TB/s, SM count."""
+    import torch
+    buf = torch.empty(64 << 20, dtype=torch.uint8, device="cuda")
+    out = np.zeros(5)
+    sh, _ = _stream_handle(stream)
+    _check(lib().bdc_measure_peaks(ctypes.c_void_p(buf.data_ptr()), buf.numel(), sh, _np_ptr(out)))
+    return {"fp32_tops": float(out[0]), "fp64_tops": float(out[1]), "l2_read_gbs": float(out[2]),
+            "smem_tbs": float(out[3]), "sms": int(out[4])}

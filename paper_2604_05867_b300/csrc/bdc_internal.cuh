@@ -117,6 +117,7 @@ struct bdc_engine {
     // d-free precompute
     int64_t R = 0;          // number of input orbit representatives
     int64_t Rout = 0;       // number of output orbit classes (all lengths)
+    uint32_t *pflags = nullptr;  // [nd] checks of a p given by bdc_set_p (bit 0 invalid, 1 not cpl-, 2 not rev-invariant)
     uint32_t *reps = nullptr;   // [R] sorted
     uint8_t *osize = nullptr;   // [R]
     uint32_t *Nk = nullptr;     // [R][n+1]

@@ -132,6 +132,51 @@ __global__ void k_check_given_q(const double *q, size_t M, double *inst) {
     }
 }
 
+// checks of an input distribution given by the caller (instance z = blockIdx.y):
+// flags[z] |= 1 if an entry is negative or not finite, 2 if p(x) != p(cpl x)
+// for some x, 4 if p(x) != p(rev x); block sums of p into part slot 0
+__global__ void k_check_p(int n, const double *p, uint32_t *flags, double *part, int maxblk) {
+    __shared__ double red[32];
+    const int z = blockIdx.y;
+    const size_t N = (size_t)1 << n, full = N - 1;
+    const double *pz = p + z * N;
+    uint32_t f = 0;
+    double s = 0.0;
+    for (size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x; x < N; x += (size_t)gridDim.x * blockDim.x) {
+        const double v = pz[x];
+        if (!(v >= 0.0) || !isfinite(v)) f |= 1u;
+        if (v != pz[x ^ full]) f |= 2u;
+        if (v != pz[rev_bits((uint32_t)x, n)]) f |= 4u;
+        s += v;
+    }
+    f = __reduce_or_sync(0xffffffffu, f);
+    if ((threadIdx.x & 31) == 0 && f) atomicOr(flags + z, f);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[w];
+        part[((size_t)z * 2 + 0) * maxblk * 4 + blockIdx.x * 4] = t;
+    }
+}
+
+// p <- p / sum p per instance, the sum taken from the nb block partials of
+// k_check_p (in block order: every CTA forms the same value)
+__global__ void k_normalize_p(int n, double *p, const double *part, int maxblk, int nb) {
+    __shared__ double red[FIN_THREADS / 32];
+    __shared__ double tot_s;
+    const int z = blockIdx.y;
+    const double tot = fin_sum(part + ((size_t)z * 2 + 0) * maxblk * 4, 4, nb, red);
+    if (threadIdx.x == 0) tot_s = tot;
+    __syncthreads();
+    const double t = tot_s;
+    const size_t N = (size_t)1 << n;
+    double *pz = p + z * N;
+    for (size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x; x < N; x += (size_t)gridDim.x * blockDim.x)
+        pz[x] = pz[x] / t;
+}
+
 // certified upper bound: U = max_x up(D'_x + m_x) + up(log2 sum q~ + e_Lambda)
 __global__ void k_finalize_cert(int nd, const double *part, int maxblk, int nb0, int nb1, double Kterms,
                                 int have_lower, double *inst) {
@@ -222,6 +267,7 @@ size_t carve(bdc_engine *e, char *base) {
     e->oreps = c.take<uint32_t>(e->Rout);
     e->ocls = c.take<int32_t>(M);
     e->counter = c.take<uint32_t>(64 + 2 * (size_t)nd);
+    e->pflags = c.take<uint32_t>((size_t)nd);
     e->scan_tmp = c.take<uint32_t>(M / 2048 + 16);
     e->bk = c.take<double>((size_t)6 * nd * (n + 1));
     e->tab_clog = c.take<double>(8192);
@@ -1031,34 +1077,47 @@ static bdc_status download_p(bdc_engine *e, double *p_host, bool normalize) {
     return BDC_OK;
 }
 
-// set p of every representation (FP64 copy exact; FP32 rounded), no pending update
+// set p of every representation (FP64 copy exact; FP32 rounded), no pending
+// update.  The host array is copied into a scratch area of the workspace and
+// checked there on the device (finite, non-negative, positive sum, and the
+// invariances the half mode, the orbit mean and the literal path rely on);
+// only a valid p replaces the engine's.
 static bdc_status upload_p(bdc_engine *e, const double *p_host, bool normalize) {
-    const size_t N = (size_t)1 << e->n, cnt = N * e->nd;
-    std::vector<double> p(p_host, p_host + cnt);
-    for (int z = 0; z < e->nd; z++) {
+    const int n = e->n, nd = e->nd;
+    const size_t N = (size_t)1 << n, cnt = N * nd;
+    const int maxblk = part_maxblk(e);
+    double *scratch = e->marg;  // [nd][2^n] doubles, free between calls
+    double *part = e->f64.part;
+    const int nb = std::min(maxblk, grid_for(N, 256, 1024));
+    BDC_CUDA_TRY(cudaMemcpyAsync(scratch, p_host, cnt * sizeof(double), cudaMemcpyHostToDevice, e->stream));
+    BDC_CUDA_TRY(cudaMemsetAsync(e->pflags, 0, nd * sizeof(uint32_t), e->stream));
+    k_check_p<<<dim3(nb, nd), 256, 0, e->stream>>>(n, scratch, e->pflags, part, maxblk); e->launches++;
+    BDC_CUDA_TRY(cudaGetLastError());
+    std::vector<uint32_t> flags(nd);
+    std::vector<double> sums((size_t)nd * nb);
+    BDC_CUDA_TRY(cudaMemcpyAsync(flags.data(), e->pflags, nd * sizeof(uint32_t), cudaMemcpyDeviceToHost, e->stream));
+    for (int z = 0; z < nd; z++)
+        BDC_CUDA_TRY(cudaMemcpy2DAsync(sums.data() + (size_t)z * nb, sizeof(double),
+                                       part + (size_t)z * 2 * maxblk * 4, 4 * sizeof(double), sizeof(double), nb,
+                                       cudaMemcpyDeviceToHost, e->stream));
+    BDC_TRY(sync_check(e, "bdc_set_p checks"));
+    bool sym = true, orb = true;
+    for (int z = 0; z < nd; z++) {
+        if (flags[z] & 1u) BDC_FAIL(BDC_EINVAL, "bdc_set_p: entries must be finite and non-negative");
         double s = 0.0;
-        for (size_t x = 0; x < N; x++) {
-            if (!(p[z * N + x] >= 0.0) || !std::isfinite(p[z * N + x]))
-                BDC_FAIL(BDC_EINVAL, "bdc_set_p: entries must be finite and non-negative");
-            s += p[z * N + x];
-        }
-        if (!(s > 0.0)) BDC_FAIL(BDC_EINVAL, "bdc_set_p: every instance needs a positive sum");
-        if (normalize)
-            for (size_t x = 0; x < N; x++) p[z * N + x] /= s;
+        for (int b = 0; b < nb; b++) s += sums[(size_t)z * nb + b];
+        if (!(s > 0.0) || !std::isfinite(s)) BDC_FAIL(BDC_EINVAL, "bdc_set_p: every instance needs a positive sum");
+        sym = sym && !(flags[z] & 2u);
+        orb = orb && !(flags[z] & 4u);
+    }
+    if (normalize) {
+        k_normalize_p<<<dim3(grid_for(N, 256, 1024), nd), FIN_THREADS, 0, e->stream>>>(n, scratch, part, maxblk, nb);
+        e->launches++;
+        BDC_CUDA_TRY(cudaGetLastError());
     }
     // complement half mode needs p(x) == p(cpl x) exactly; the orbit mean of D
     // and the literal path (work on orbit representatives) need invariance
     // under reversal too
-    bool sym = true, orb = true;
-    const size_t full = N - 1;
-    const int n = e->n;
-    for (size_t i = 0; i < cnt && (sym || orb); i++) {
-        const size_t base = i & ~full, x = i & full;
-        size_t rx = 0;
-        for (int t = 0; t < n; t++) rx |= ((x >> t) & 1u) << (n - 1 - t);
-        sym = sym && p[i] == p[base | (x ^ full)];
-        orb = orb && p[i] == p[base | rx];
-    }
     orb = orb && sym;
     if (sym != e->half_ok || orb != e->orbit_ok) drop_graphs(e);
     e->half_ok = sym;
@@ -1066,7 +1125,7 @@ static bdc_status upload_p(bdc_engine *e, const double *p_host, bool normalize) 
     e->half_active[0] = e->half_active[1] = false;
     e->f1_current[0] = e->f1_current[1] = false;
     e->p_unsym[0] = e->p_unsym[1] = false;
-    BDC_CUDA_TRY(cudaMemcpyAsync(e->f64.p, p.data(), cnt * sizeof(double), cudaMemcpyHostToDevice, e->stream));
+    BDC_CUDA_TRY(cudaMemcpyAsync(e->f64.p, scratch, cnt * sizeof(double), cudaMemcpyDeviceToDevice, e->stream));
     BDC_TRY(sync_check(e, "bdc_set_p upload"));
     const int g = grid_for(cnt, 256);
     k_convert<double, float><<<g, 256, 0, e->stream>>>(e->f64.p, e->f32.p, cnt); e->launches++;

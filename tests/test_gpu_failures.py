@@ -1,8 +1,8 @@
 """Failure paths reported as status codes, without any GPU fault.
 
 - BDC_ENONFINITE: an input distribution with zero mass on every input but
-  one leaves outputs with q(y) = 0 that other inputs reach, so D_x = +Inf
-  reaches the bounds' reductions; a NaN placed by the host into a given q
+  one leaves outputs with q(y) = 0 that other inputs reach, so (with the
+  floor under q switched off) D_x = +Inf reaches the bounds' reductions; a NaN placed by the host into a given q
   reaches the certificate.  The instance stops, the call returns the status,
   and the engine and the CUDA context stay usable.
 - BDC_EINVAL from the device check of a given q that is not positive.
@@ -26,7 +26,8 @@ def _bdc():
 def test_zero_mass_input_gives_nonfinite_status_and_engine_recovers():
     bdc = _bdc()
     n, d = 10, 0.5
-    eng = bdc.Engine(n, [d, 0.3], options=bdc.default_options(enable_literal=0))
+    # q_floor = 0: no floor under the output marginal before its log
+    eng = bdc.Engine(n, [d, 0.3], options=bdc.default_options(enable_literal=0, q_floor=0.0))
     p = np.full((2, 1 << n), 1.0 / (1 << n))
     p[0] = 0.0
     p[0, 0] = 1.0  # all mass on 0^n: outputs containing a 1 get q = 0
