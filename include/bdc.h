@@ -69,7 +69,10 @@ typedef struct {
      * certified output distribution is positive everywhere.  Default 2^-30. */
     double certify_mix;
     /* Row-sweep length n2 and column tile width override for the sweep
-     * schedule (0 = automatic). */
+     * schedule (0 = automatic; a negative n2 selects the streaming schedule,
+     * one global-memory pass per input symbol, which is what the automatic
+     * choice is for FP64 at n >= 27, where no shared-memory tile split
+     * exists). */
     int sched_n2_fp32, sched_w_fp32, sched_n2_fp64, sched_w_fp64;
     /* Reserve the buffers of the literal (enumeration) path.  Default 1. */
     int enable_literal;
@@ -113,7 +116,7 @@ void bdc_default_options(bdc_options *opt);
 
 /* --- lifecycle ---------------------------------------------------------- */
 
-/* Create an engine for input length n (1 <= n <= 26) and nd >= 1 deletion
+/* Create an engine for input length n (1 <= n <= 28) and nd >= 1 deletion
  * probabilities d[0..nd) in [0,1] (copied).  opt may be NULL (defaults).
  * Runs no kernel.  *out is owned by the caller (bdc_destroy). */
 bdc_status bdc_create(int n, const double *d, int nd, const bdc_options *opt, bdc_engine **out);
@@ -294,7 +297,7 @@ bdc_status bdc_profile_iteration(bdc_engine *eng, int precision, int impl, int r
 bdc_status bdc_measure_peaks(void *scratch_dev, size_t bytes, void *cuda_stream, double *out);
 
 /* Schedule of the sweep in `precision`: input split n1 + n2 (n2 = 0: one
- * pass) and the column tile width. */
+ * pass; n2 = -1: the streaming schedule) and the column tile width. */
 bdc_status bdc_get_schedule(const bdc_engine *eng, int precision, int *n1, int *n2, int *width);
 
 /* Autotune the sweep schedule of `precision` on this engine: time `reps`

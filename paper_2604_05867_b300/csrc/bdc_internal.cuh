@@ -17,7 +17,7 @@
 
 #include "../../include/bdc.h"
 
-#define BDC_MAXN 26
+#define BDC_MAXN 28
 #define BDC_HIST 8192
 
 // ---------------------------------------------------------------------------
@@ -79,6 +79,8 @@ enum {
 // pass); n2 == 0 means a single in-CTA pass over all n symbols.
 // ---------------------------------------------------------------------------
 struct Sched {
+    // n2 < 0: the streaming schedule (one global-memory pass per input
+    // symbol), for sizes whose tiles do not fit in shared memory
     int n1, n2, lw;  // lw = log2 of the column tile width
     int nblk_cols;   // CTAs per instance of the columns passes
 };
@@ -198,6 +200,11 @@ bool step_possible(const bdc_engine *e, const Sched &s);
 // BA glue (ba.cu)
 template <typename T>
 bdc_status launch_build_Hb(bdc_engine *e, PrecBuf<T> &b);
+// level-by-level sweeps through global memory (the streaming schedule, n2 < 0)
+template <typename T>
+bdc_status stream_forward(bdc_engine *e, PrecBuf<T> &b, const T *p_src, int apply_update, int mode);
+template <typename T>
+bdc_status stream_adjoint(bdc_engine *e, PrecBuf<T> &b, const T *Lsrc, const T *omega, T *Dout, int mode);
 bdc_status launch_build_Hb_w(bdc_engine *e, const double *w, double *out);
 template <typename T>
 bdc_status launch_finalize(bdc_engine *e, PrecBuf<T> &b, int mode, int add_negh = 0, int nblk = 0, int stepped = 0);

@@ -243,8 +243,9 @@ void carve_prec(Carver &c, PrecBuf<T> &b, int n, int nd, int maxblk) {
     b.omega = c.take<T>((size_t)nd * (n + 1));
     b.omega2 = c.take<T>((size_t)nd * (n + 1));
     b.part = c.take<double>((size_t)nd * 2 * maxblk * 4);
-    if (b.s.n2 > 0 || n >= 15) {
-        // sized for every split the autotuner may choose (n2 >= 8, so n1 <= n - 8)
+    if (b.s.n2 != 0 || n >= 15) {
+        // sized for every split the autotuner may choose (n2 >= 8, so n1 <= n - 8);
+        // the streaming schedule (n2 < 0) ping-pongs between Tm and Gb
         int n1max = std::max(b.s.n2 > 0 ? b.s.n1 : 0, n - 8);
         b.F1 = c.take<T>(nd * N);
         b.Tm = c.take<T>(nd * M);
@@ -314,7 +315,7 @@ static bdc_engine *new_engine(int n, int nd, const bdc_options *opt);
 extern "C" bdc_status bdc_create(int n, const double *d, int nd, const bdc_options *opt, bdc_engine **out) {
     if (!out) BDC_FAIL(BDC_EINVAL, "bdc_create: out is NULL");
     *out = nullptr;
-    if (n < 1 || n > BDC_MAXN) BDC_FAIL(BDC_EINVAL, "bdc_create: n must be in [1, 26]");
+    if (n < 1 || n > BDC_MAXN) BDC_FAIL(BDC_EINVAL, "bdc_create: n must be in [1, 28]");
     if (!d || nd < 1 || nd > 4096) BDC_FAIL(BDC_EINVAL, "bdc_create: need 1 <= nd <= 4096 values of d");
     for (int i = 0; i < nd; i++)
         if (!(d[i] >= 0.0 && d[i] <= 1.0)) BDC_FAIL(BDC_EINVAL, "bdc_create: every d must lie in [0, 1]");
@@ -327,7 +328,7 @@ extern "C" bdc_status bdc_create(int n, const double *d, int nd, const bdc_optio
 extern "C" bdc_status bdc_create_lengths(int n, const double *b, int nb, const bdc_options *opt, bdc_engine **out) {
     if (!out) BDC_FAIL(BDC_EINVAL, "bdc_create_lengths: out is NULL");
     *out = nullptr;
-    if (n < 1 || n > BDC_MAXN) BDC_FAIL(BDC_EINVAL, "bdc_create_lengths: n must be in [1, 26]");
+    if (n < 1 || n > BDC_MAXN) BDC_FAIL(BDC_EINVAL, "bdc_create_lengths: n must be in [1, 28]");
     if (!b || nb < 1 || nb > 4096) BDC_FAIL(BDC_EINVAL, "bdc_create_lengths: need 1 <= nb <= 4096 length distributions");
     std::vector<double> bl((size_t)nb * (n + 1));
     for (int z = 0; z < nb; z++) {
@@ -1306,7 +1307,7 @@ extern "C" bdc_status bdc_load(bdc_engine *e, const char *path) {
 // ---------------------------------------------------------------------------
 extern "C" bdc_status bdc_subseq_counts(int n, const uint64_t *x_dev, int64_t nx, uint64_t *N_dev, double *S_dev,
                                         uint64_t *emb_dev, void *stream) {
-    if (n < 1 || n > BDC_MAXN) BDC_FAIL(BDC_EINVAL, "bdc_subseq_counts: n must be in [1, 26]");
+    if (n < 1 || n > BDC_MAXN) BDC_FAIL(BDC_EINVAL, "bdc_subseq_counts: n must be in [1, 28]");
     if (!x_dev || nx < 0 || (!N_dev && nx > 0)) BDC_FAIL(BDC_EINVAL, "bdc_subseq_counts: bad arguments");
     if (nx == 0) return BDC_OK;
     cudaStream_t st = (cudaStream_t)stream;
@@ -1404,8 +1405,10 @@ extern "C" bdc_status bdc_autotune(bdc_engine *e, int prec, int reps, int n2, in
         // set a known schedule (e.g. from a cache) instead of searching
         Sched s = make_sched(e->n, prec == BDC_FP32 ? 4 : 8, n2, width);
         const size_t tile = (prec == BDC_FP32) ? 32768 : 16384;
-        if (e->n < 15 || s.n2 < 8 || s.n2 > 14 || ((size_t)2 << s.n1 << s.lw) > tile || s.nblk_cols > part_maxblk(e))
-            BDC_FAIL(BDC_EINVAL, "bdc_autotune: schedule outside the reserved buffers (n >= 15, 8 <= n2 <= 14, tile)");
+        if (e->n < 15 || s.n2 < 8 || s.n2 > 14 || ((size_t)2 << s.n1 << s.lw) > tile || ((size_t)2 << s.n2) > tile ||
+            s.nblk_cols > part_maxblk(e))
+            BDC_FAIL(BDC_EINVAL, "bdc_autotune: schedule outside the reserved buffers (n >= 15, 8 <= n2 <= 14, "
+                                 "column and row tiles within shared memory)");
         PrecBuf<float> &f = e->f32;
         PrecBuf<double> &d = e->f64;
         if (prec == BDC_FP32) f.s = s;

@@ -20,7 +20,7 @@
 namespace {
 
 constexpr int WARPS_PER_CTA = 8;
-constexpr int STK = 28;  // >= BDC_MAXN + 2
+constexpr int STK = 30;  // >= BDC_MAXN + 2
 
 __device__ __forceinline__ uint32_t warp_excl_scan(uint32_t v, int lane) {
     uint32_t s = v;

@@ -1794,7 +1794,7 @@ SweepArgs make_args(bdc_engine *e, PrecBuf<T> &b) {
     a.q_floor_f = (float)e->opt.q_floor;
     a.tma_polls = e->opt.tma_wait_polls == 0 ? (1u << 22)
                                              : (e->opt.tma_wait_polls < 0 ? 0u : (uint32_t)e->opt.tma_wait_polls);
-    double c = 1.0;  // C(n,k), exact in double for n <= 26
+    double c = 1.0;  // C(n,k), exact in double for n <= 28
     for (int k = 0; k <= e->n; k++) {
         a.inv_binom_f[k] = (float)(1.0 / c);
         c = c * (e->n - k) / (k + 1);
@@ -1874,6 +1874,15 @@ Sched make_sched(int n, int elem_bytes, int n2_override, int w_override) {
     const int tile = (elem_bytes == 4) ? 32768 : 16384;  // elements per CTA tile (128 KB)
     int nsingle = 0;
     while ((2 << (nsingle + 1)) <= tile) nsingle++;       // 2^(n+1) <= tile
+    // the streaming schedule: asked for (n2_override < 0), or no split of n
+    // into column and row tiles of at most `tile` elements exists (n > 2 nsingle)
+    if (n2_override < 0 || (n > 2 * nsingle && n2_override == 0)) {
+        s.n1 = n;
+        s.n2 = -1;
+        s.lw = 0;
+        s.nblk_cols = 1024;  // CTAs of the streaming epilogues (block partials per instance)
+        return s;
+    }
     if (n <= nsingle && n2_override == 0) {
         s.n1 = n;
         s.n2 = 0;
@@ -1887,6 +1896,13 @@ Sched make_sched(int n, int elem_bytes, int n2_override, int w_override) {
     int n2 = n2_override ? n2_override : std::min(n - 1, n2max);
     if (n2 < 5) n2 = std::min(5, n - 1);
     if (n - n2 > nsingle) n2 = n - nsingle;  // the columns tile must hold 2^(n1+1) rows
+    if (((size_t)2 << n2) > (size_t)tile) {   // nor can a row tile hold 2^(n2+1): stream
+        s.n1 = n;
+        s.n2 = -1;
+        s.lw = 0;
+        s.nblk_cols = 1024;
+        return s;
+    }
     s.n2 = n2;
     s.n1 = n - n2;
     int lw = 0;
@@ -1981,6 +1997,7 @@ bool step_possible(const bdc_engine *e, const Sched &s) {
 template <typename T>
 bdc_status sweep_forward(bdc_engine *e, PrecBuf<T> &b, const T *p_src, int apply_update, int mode, bool half,
                          bool sym_rev, bool cols, bool rest) {
+    if (b.s.n2 < 0) return stream_forward<T>(e, b, p_src, apply_update, mode);
     SweepArgs a = make_args(e, b);
     const Sched &s = b.s;
     half = half && half_possible(s);
@@ -2042,6 +2059,7 @@ bdc_status sweep_forward(bdc_engine *e, PrecBuf<T> &b, const T *p_src, int apply
 template <typename T>
 bdc_status sweep_adjoint(bdc_engine *e, PrecBuf<T> &b, const T *Lsrc, const T *omega, T *Dout, int mode, bool half,
                          bool step, bool keep_p) {
+    if (b.s.n2 < 0) return stream_adjoint<T>(e, b, Lsrc, omega, Dout, mode);
     SweepArgs a = make_args(e, b);
     const Sched &s = b.s;
     half = half && half_possible(s);

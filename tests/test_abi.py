@@ -40,7 +40,7 @@ def test_create_validates_without_gpu():
     h = ctypes.c_void_p()
     d = (ctypes.c_double * 1)(0.5)
     assert L.bdc_create(0, ctypes.cast(d, ctypes.c_void_p), 1, None, ctypes.byref(h)) == -1
-    assert L.bdc_create(27, ctypes.cast(d, ctypes.c_void_p), 1, None, ctypes.byref(h)) == -1
+    assert L.bdc_create(29, ctypes.cast(d, ctypes.c_void_p), 1, None, ctypes.byref(h)) == -1
     bad = (ctypes.c_double * 1)(1.5)
     assert L.bdc_create(10, ctypes.cast(bad, ctypes.c_void_p), 1, None, ctypes.byref(h)) == -1
     assert b"[0, 1]" in L.bdc_last_error()
@@ -64,3 +64,27 @@ def test_sched_and_workspace_scale():
         sizes.append(L.bdc_workspace_bytes(h))
         L.bdc_destroy(h)
     assert sizes[0] < sizes[1] < sizes[2]
+
+
+@pytest.mark.parametrize("n", [26, 27, 28])
+def test_schedules_up_to_n28(n):
+    # FP32 splits n into shared-memory column and row tiles up to n = 28; FP64
+    # (half the elements per tile) only up to n = 26, and streams beyond; the
+    # workspace of one instance stays within the device's memory
+    import paper_2604_05867_b300 as bdc
+    L = bdc.lib()
+    d = (ctypes.c_double * 1)(0.5)
+    opt = bdc.default_options(enable_literal=0)
+    h = ctypes.c_void_p()
+    assert L.bdc_create(n, ctypes.cast(d, ctypes.c_void_p), 1, ctypes.byref(opt), ctypes.byref(h)) == 0
+    n1, n2, w = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    assert L.bdc_get_schedule(h, 0, ctypes.byref(n1), ctypes.byref(n2), ctypes.byref(w)) == 0
+    assert n2.value > 0 and n1.value + n2.value == n
+    assert (2 << n1.value) * w.value <= 32768 and (2 << n2.value) <= 32768
+    assert L.bdc_get_schedule(h, 1, ctypes.byref(n1), ctypes.byref(n2), ctypes.byref(w)) == 0
+    if n <= 26:
+        assert n2.value > 0 and (2 << n1.value) * w.value <= 16384 and (2 << n2.value) <= 16384
+    else:
+        assert n2.value == -1
+    assert L.bdc_workspace_bytes(h) < 200e9
+    L.bdc_destroy(h)
