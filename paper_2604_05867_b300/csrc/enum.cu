@@ -272,16 +272,11 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
                 sp++;
             }
         }
-        while (sp > 0) {
-            sp--;
-            uint32_t E = stkE[wid][sp][lane];
-            uint32_t code = __shfl_sync(FULL, stk_code, sp);
-            uint32_t cnt = __shfl_sync(FULL, stk_cnt, sp);
-            int k = bitlen32(code) - 1;
-            // record (code, k, cnt)
+        // record one node (code, length kk, count cnt); all lanes call it
+        auto record = [&](uint32_t code, int kk, uint32_t cnt) {
             if (MODE == WALK_STATS) {
-                if (lane == k) accN++;
-                if (lane == nbuf) { bcode = (uint32_t)k; bcnt = cnt; }
+                if (lane == kk) accN++;
+                if (lane == nbuf) { bcode = (uint32_t)kk; bcnt = cnt; }
                 if (++nbuf == 32) {
                     unsigned long long hi, lo;
                     clog2c_parts(bcnt, a.tabfix, hi, lo);
@@ -297,15 +292,24 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
                 if (lane == nbuf) { bcode = code; bcnt = cnt; }
                 nbuf++;
                 if (nbuf == 32) {
-                    int kk = bitlen32(bcode) - 1;
-                    double w = (double)bcnt * kw[kk];
+                    int k2 = bitlen32(bcode) - 1;
+                    double w = (double)bcnt * kw[k2];
                     if (w > 0.0) {
                         double lc = bcnt < 4096u ? __ldg(a.tab_log2 + bcnt) : log2((double)bcnt);
-                        accD += w * (lc + lkw[kk] - lb[kk] - L[bcode]);
+                        accD += w * (lc + lkw[k2] - lb[k2] - L[bcode]);
                     }
                     nbuf = 0;
                 }
             }
+        };
+        const uint32_t last_only = 1u << (n - 1);
+        while (sp > 0) {
+            sp--;
+            uint32_t E = stkE[wid][sp][lane];
+            uint32_t code = __shfl_sync(FULL, stk_code, sp);
+            uint32_t cnt = __shfl_sync(FULL, stk_cnt, sp);
+            int k = bitlen32(code) - 1;
+            record(code, k, cnt);
             if (k == n) continue;
             uint32_t S = warp_excl_scan(E, lane);
 #pragma unroll
@@ -313,9 +317,15 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
                 uint32_t Eb = (xb == b) ? S : 0u;
                 uint32_t cb = __reduce_add_sync(FULL, Eb);
                 if (cb > 0) {
-                    stkE[wid][sp][lane] = Eb;
-                    if (lane == sp) { stk_code = (code << 1) | (uint32_t)b; stk_cnt = cb; }
-                    sp++;
+                    if (__ballot_sync(FULL, Eb != 0u) == last_only) {
+                        // every embedding of the child ends at the last symbol:
+                        // it has no children, record it here instead of stacking it
+                        record((code << 1) | (uint32_t)b, k + 1, cb);
+                    } else {
+                        stkE[wid][sp][lane] = Eb;
+                        if (lane == sp) { stk_code = (code << 1) | (uint32_t)b; stk_cnt = cb; }
+                        sp++;
+                    }
                 }
             }
         }
@@ -422,7 +432,33 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_super_walk(SuperArgs a, 
             uint32_t x = prefix;
             uint32_t nb_lane = 0;
             stkM[wid][depth][lane] = M;
+            // y_{k-1} (the last symbol of y), matched by the last symbol of x
+            const int ylast = (k >= 1) ? (int)(y & 1u) : 2;
             while (true) {
+                if (depth == n - 1) {
+                    // one symbol left: both children are leaves, with counts
+                    // M'_k = M_k + [y_{k-1} = b] M_{k-1} (a leaf with count 0
+                    // does not contain y)
+                    const uint32_t mk = __shfl_sync(FULL, M, k);
+                    const uint32_t mk1 = __shfl_sync(FULL, M, k >= 1 ? k - 1 : 0);
+#pragma unroll
+                    for (int b = 0; b < 2; b++) {
+                        const uint32_t cnt = mk + ((ylast == b) ? mk1 : 0u);
+                        if (cnt) {
+                            if (lane == nbuf) { bx = (x << 1) | (uint32_t)b; bc = cnt; }
+                            nbuf++;
+                            if (nbuf == 32) {
+                                acc += p[bx] * (double)bc;
+                                nbuf = 0;
+                            }
+                        }
+                    }
+                    depth--;
+                    x >>= 1;
+                    if (depth < s) break;
+                    M = stkM[wid][depth][lane];
+                    continue;
+                }
                 if (depth == n) {
                     uint32_t cnt = __shfl_sync(FULL, M, k);
                     if (lane == nbuf) { bx = x; bc = cnt; }
