@@ -211,6 +211,7 @@ struct WalkArgs {
 
 template <int MODE>
 __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) {
+    constexpr int RZ = 4;  // subtrees spanning at most RZ positions are done in closed form (30 strings <= 32 lanes)
     __shared__ uint32_t stkE[WARPS_PER_CTA][STK][32];
     // WALK_STATS: per warp and length, the exact sums of c*log2(c) (hi, lo parts);
     // nodes are buffered 32 at a time (lane i holds the i-th) and folded in by
@@ -302,7 +303,71 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
                 }
             }
         };
-        const uint32_t last_only = 1u << (n - 1);
+        // The whole subtree below a child y' whose embeddings all end at or after
+        // position pm, r = n - 1 - pm <= RZ, in closed form, one descendant per
+        // lane: lane l stands for the string z of code l + 2 (every string of
+        // length 1..RZ in lanes 0..29) and runs the embedding DP of y' z over the
+        // last r positions, from c_0 = the embeddings of y' ending before the
+        // position (a prefix sum of E) and c_j = 0 (z_1 must come after y' ends):
+        // c_j += [x_t = z_j] c_{j-1}.  Count(y' z, x) = c_m; distinct lanes are
+        // distinct strings, and a count of 0 means z does not follow y' in x.
+        auto subtree = [&](uint32_t ccode, int kc, uint32_t Eb, int pm) {
+            const int r = n - 1 - pm;
+            uint32_t Ew[RZ + 1];
+            int xw[RZ + 1];
+#pragma unroll
+            for (int j = 0; j <= RZ; j++) {
+                Ew[j] = __shfl_sync(FULL, Eb, pm + j < 31 ? pm + j : 31);
+                xw[j] = (pm + j < n) ? (int)((x >> (n - 1 - (pm + j))) & 1u) : 2;
+            }
+            const uint32_t zc = (uint32_t)lane + 2u;
+            const int m = bitlen32(zc) - 1;
+            uint32_t c[RZ + 1];
+            c[0] = Ew[0];
+#pragma unroll
+            for (int j = 1; j <= RZ; j++) c[j] = 0u;
+#pragma unroll
+            for (int t = 1; t <= RZ; t++) {
+                if (t <= r) {
+#pragma unroll
+                    for (int j = RZ; j >= 1; j--)
+                        if (j <= m && (int)((zc >> (m - j)) & 1u) == xw[t]) c[j] += c[j - 1];
+                    c[0] += Ew[t];
+                }
+            }
+            uint32_t cnt = c[1];
+#pragma unroll
+            for (int j = 2; j <= RZ; j++)
+                if (m == j) cnt = c[j];
+            const bool valid = lane < 30 && m <= r && cnt > 0u;
+            const uint32_t dcode = (ccode << m) | (zc - (1u << m));
+            const int kk = kc + m;
+            if (MODE == WALK_STATS) {
+#pragma unroll
+                for (int mm = 1; mm <= RZ; mm++) {
+                    const int num = __popc(__ballot_sync(FULL, valid && m == mm));
+                    if (lane == kc + mm) accN += (uint32_t)num;
+                }
+                if (valid) {
+                    unsigned long long hi, lo;
+                    clog2c_parts(cnt, a.tabfix, hi, lo);
+                    if (hi | lo) {
+                        atomicAdd(&wacc[wid][kk][0], hi);
+                        atomicAdd(&wacc[wid][kk][1], lo);
+                    }
+                }
+            } else if (MODE == WALK_EMIT) {
+                if (valid) a.emb[dcode] = cnt;
+            } else {
+                if (valid) {
+                    const double w = (double)cnt * kw[kk];
+                    if (w > 0.0) {
+                        const double lc = cnt < 4096u ? __ldg(a.tab_log2 + cnt) : log2((double)cnt);
+                        accD += w * (lc + lkw[kk] - lb[kk] - L[dcode]);
+                    }
+                }
+            }
+        };
         while (sp > 0) {
             sp--;
             uint32_t E = stkE[wid][sp][lane];
@@ -317,10 +382,12 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
                 uint32_t Eb = (xb == b) ? S : 0u;
                 uint32_t cb = __reduce_add_sync(FULL, Eb);
                 if (cb > 0) {
-                    if (__ballot_sync(FULL, Eb != 0u) == last_only) {
-                        // every embedding of the child ends at the last symbol:
-                        // it has no children, record it here instead of stacking it
+                    const int pm = __ffs(__ballot_sync(FULL, Eb != 0u)) - 1;
+                    if (n - 1 - pm <= RZ) {
+                        // the child's subtree spans the last RZ positions at most:
+                        // record it and all its descendants here instead of stacking it
                         record((code << 1) | (uint32_t)b, k + 1, cb);
+                        subtree((code << 1) | (uint32_t)b, k + 1, Eb, pm);
                     } else {
                         stkE[wid][sp][lane] = Eb;
                         if (lane == sp) { stk_code = (code << 1) | (uint32_t)b; stk_cnt = cb; }
@@ -390,6 +457,7 @@ struct SuperArgs {
 };
 
 __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_super_walk(SuperArgs a, uint32_t *counter) {
+    constexpr int RB = 5;  // levels below the walk, evaluated one leaf per lane (2^RB = 32)
     __shared__ uint32_t stkM[WARPS_PER_CTA][STK][32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const unsigned FULL = 0xffffffffu;
@@ -423,80 +491,81 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_super_walk(SuperArgs a, 
             if (m + (n - i - 1) < k) { alive = false; break; }
         }
         double acc = 0.0;
-        uint32_t bx = 0, bc = 0;
-        int nbuf = 0;
         if (alive) {
-            // iterative walk from depth s; lane t holds the next child to try
-            // at depth t, stkM[t] the embedding vector of the prefix of length t
-            int depth = s;
-            uint32_t x = prefix;
-            uint32_t nb_lane = 0;
-            stkM[wid][depth][lane] = M;
-            // y_{k-1} (the last symbol of y), matched by the last symbol of x
-            const int ylast = (k >= 1) ? (int)(y & 1u) : 2;
-            while (true) {
-                if (depth == n - 1) {
-                    // one symbol left: both children are leaves, with counts
-                    // M'_k = M_k + [y_{k-1} = b] M_{k-1} (a leaf with count 0
-                    // does not contain y)
-                    const uint32_t mk = __shfl_sync(FULL, M, k);
-                    const uint32_t mk1 = __shfl_sync(FULL, M, k >= 1 ? k - 1 : 0);
+            // The last r <= RB levels in closed form, one leaf per lane: lane t
+            // appends the r symbols of t (most significant first) to the prefix
+            // and carries the window w[j] = M_{k-RB+j}, j = 0..RB, through them:
+            // M'_i = M_i + [y_{i-1} = b] M_{i-1}.  After r steps w[RB] = M_k is
+            // the leaf's embedding count (0: not a supersequence); a window entry
+            // that misses its update from below the window is wrong after one
+            // step and the error climbs one entry per step, so it never reaches
+            // w[RB] within r <= RB steps.
+            // yw[j]: the symbol y_{i-1} of window entry i = k-RB+j (2: none, i <= 0)
+            int yw[RB + 1];
 #pragma unroll
-                    for (int b = 0; b < 2; b++) {
-                        const uint32_t cnt = mk + ((ylast == b) ? mk1 : 0u);
-                        if (cnt) {
-                            if (lane == nbuf) { bx = (x << 1) | (uint32_t)b; bc = cnt; }
-                            nbuf++;
-                            if (nbuf == 32) {
-                                acc += p[bx] * (double)bc;
-                                nbuf = 0;
-                            }
-                        }
+            for (int j = 0; j <= RB; j++) {
+                const int i = k - RB + j;
+                yw[j] = (i >= 1) ? (int)((y >> (k - i)) & 1u) : 2;
+            }
+            const int dstop = (n - RB > s) ? n - RB : s;  // the depth where the closed form takes over
+            auto leaves = [&](uint32_t Mv, uint32_t xpre, int r) {
+                uint32_t w[RB + 1];
+#pragma unroll
+                for (int j = 0; j <= RB; j++) {
+                    const int i = k - RB + j;
+                    w[j] = __shfl_sync(FULL, Mv, i >= 0 ? i : 0);
+                    if (i < 0) w[j] = 0u;
+                }
+#pragma unroll
+                for (int st = 0; st < RB; st++) {
+                    if (st < r) {
+                        const int b = (lane >> (r - 1 - st)) & 1;
+#pragma unroll
+                        for (int j = RB; j >= 1; j--)
+                            if (yw[j] == b) w[j] += w[j - 1];
                     }
-                    depth--;
-                    x >>= 1;
-                    if (depth < s) break;
-                    M = stkM[wid][depth][lane];
-                    continue;
                 }
-                if (depth == n) {
-                    uint32_t cnt = __shfl_sync(FULL, M, k);
-                    if (lane == nbuf) { bx = x; bc = cnt; }
-                    nbuf++;
-                    if (nbuf == 32) {
-                        acc += p[bx] * (double)bc;
-                        nbuf = 0;
+                const uint32_t cnt = w[RB];
+                if (lane < (1 << r) && cnt) acc += p[((size_t)xpre << r) | (uint32_t)lane] * (double)cnt;
+            };
+            if (dstop == s) {
+                leaves(M, prefix, n - s);
+            } else {
+                // depth-first from depth s down to dstop - 1; lane t holds the next
+                // child to try at depth t, stkM[t] the embedding vector of the
+                // prefix of length t; a completable child at depth dstop goes to
+                // the closed form
+                int depth = s;
+                uint32_t x = prefix;
+                uint32_t nb_lane = 0;
+                stkM[wid][depth][lane] = M;
+                while (true) {
+                    int b = (int)__shfl_sync(FULL, nb_lane, depth);
+                    if (b > 1) {
+                        depth--;
+                        x >>= 1;
+                        if (depth < s) break;
+                        M = stkM[wid][depth][lane];
+                        continue;
                     }
-                    depth--;
-                    x >>= 1;
-                    if (depth < s) break;
-                    M = stkM[wid][depth][lane];
-                    continue;
-                }
-                int b = (int)__shfl_sync(FULL, nb_lane, depth);
-                if (b > 1) {
-                    depth--;
-                    x >>= 1;
-                    if (depth < s) break;
-                    M = stkM[wid][depth][lane];
-                    continue;
-                }
-                if (lane == depth) nb_lane = (uint32_t)(b + 1);
-                uint32_t up = __shfl_up_sync(FULL, M, 1);
-                uint32_t Mc = M + ((ysym == b) ? up : 0u);
-                uint32_t bal = __ballot_sync(FULL, Mc > 0u && lane <= k);
-                int m = 31 - __clz(bal);
-                if (m + (n - depth - 1) < k) continue;  // not completable: prune
-                depth++;
-                x = (x << 1) | (uint32_t)b;
-                M = Mc;
-                if (depth < n) {
+                    if (lane == depth) nb_lane = (uint32_t)(b + 1);
+                    uint32_t up = __shfl_up_sync(FULL, M, 1);
+                    uint32_t Mc = M + ((ysym == b) ? up : 0u);
+                    uint32_t bal = __ballot_sync(FULL, Mc > 0u && lane <= k);
+                    int m = 31 - __clz(bal);
+                    if (m + (n - depth - 1) < k) continue;  // not completable: prune
+                    if (depth + 1 == dstop) {
+                        leaves(Mc, (x << 1) | (uint32_t)b, n - dstop);
+                        continue;
+                    }
+                    depth++;
+                    x = (x << 1) | (uint32_t)b;
+                    M = Mc;
                     stkM[wid][depth][lane] = M;
                     if (lane == depth) nb_lane = 0;
                 }
             }
         }
-        if (lane < nbuf) acc += p[bx] * (double)bc;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
         if (lane == 0) a.part[(size_t)z * a.nitems + item] = acc;
