@@ -203,6 +203,8 @@ struct WalkArgs {
     const double *kw;           // [nd][n+1] d^(n-k)(1-d)^k
     const double *lkw;          // [nd][n+1] log2 of kw (or 0 where kw == 0)
     const double *lb;           // [nd][n+1] log2 b_k
+    const double *bk;           // [nd][n+1] b_k
+    const double *l2c;          // [nd][n+1] log2 C(n,k)
     double *Dout;               // [nd][count]
     const double *inst;
     // WALK_EMIT
@@ -216,7 +218,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
     // WALK_STATS: per warp and length, the exact sums of c*log2(c) (hi, lo parts);
     // nodes are buffered 32 at a time (lane i holds the i-th) and folded in by
     // all lanes at once
-    __shared__ unsigned long long wacc[MODE == WALK_STATS ? WARPS_PER_CTA : 1][BDC_MAXN + 1][2];
+    __shared__ unsigned long long wacc[MODE == WALK_EMIT ? 1 : WARPS_PER_CTA][BDC_MAXN + 1][2];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int n = a.n;
     const int z = blockIdx.y;  // instance (literal D)
@@ -224,9 +226,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
     if (MODE == WALK_LITERAL_D && a.inst[z * INST_STRIDE + I_ACTIVE] == 0.0) return;
     const double *L = (MODE == WALK_LITERAL_D) ? a.L + ((size_t)z << (n + 1)) : nullptr;
     const double *kw = (MODE == WALK_LITERAL_D) ? a.kw + z * (n + 1) : nullptr;
-    const double *lkw = (MODE == WALK_LITERAL_D) ? a.lkw + z * (n + 1) : nullptr;
-    const double *lb = (MODE == WALK_LITERAL_D) ? a.lb + z * (n + 1) : nullptr;
-    if (MODE == WALK_STATS && lane <= BDC_MAXN) {
+    if (MODE != WALK_EMIT && lane <= BDC_MAXN) {
         wacc[wid][lane][0] = 0ull;
         wacc[wid][lane][1] = 0ull;
     }
@@ -258,9 +258,9 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
         int sp = 0;
         if (MODE == WALK_EMIT && lane == 0) a.emb[1] = 1;
         if (MODE == WALK_LITERAL_D) {
-            // empty output: count 1, weight d^n
+            // empty output: count 1, weight kw_0 (its count*log2 count is 0)
             double w = kw[0];
-            if (lane == 0 && w > 0.0) accD += w * (lkw[0] - lb[0] - L[1]);
+            if (lane == 0 && w > 0.0) accD += w * L[1];
         }
         // root children
 #pragma unroll
@@ -290,14 +290,20 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
             } else if (MODE == WALK_EMIT) {
                 if (lane == 0) a.emb[code] = cnt;
             } else {
+                // D_x = sum_k [kw_k S_k(x) - b_k log2 C(n,k)] - sum_y kw_|y| Count(y,x) L(y):
+                // per node the cross term in FP64 and count*log2(count) in exact
+                // fixed point per length, as in the statistics walk
                 if (lane == nbuf) { bcode = code; bcnt = cnt; }
                 nbuf++;
                 if (nbuf == 32) {
-                    int k2 = bitlen32(bcode) - 1;
-                    double w = (double)bcnt * kw[k2];
-                    if (w > 0.0) {
-                        double lc = bcnt < 4096u ? __ldg(a.tab_log2 + bcnt) : log2((double)bcnt);
-                        accD += w * (lc + lkw[k2] - lb[k2] - L[bcode]);
+                    const int k2 = bitlen32(bcode) - 1;
+                    const double w = (double)bcnt * kw[k2];
+                    if (w > 0.0) accD += w * L[bcode];
+                    unsigned long long hi, lo;
+                    clog2c_parts(bcnt, a.tabfix, hi, lo);
+                    if (hi | lo) {
+                        atomicAdd(&wacc[wid][k2][0], hi);
+                        atomicAdd(&wacc[wid][k2][1], lo);
                     }
                     nbuf = 0;
                 }
@@ -361,9 +367,12 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
             } else {
                 if (valid) {
                     const double w = (double)cnt * kw[kk];
-                    if (w > 0.0) {
-                        const double lc = cnt < 4096u ? __ldg(a.tab_log2 + cnt) : log2((double)cnt);
-                        accD += w * (lc + lkw[kk] - lb[kk] - L[dcode]);
+                    if (w > 0.0) accD += w * L[dcode];
+                    unsigned long long hi, lo;
+                    clog2c_parts(cnt, a.tabfix, hi, lo);
+                    if (hi | lo) {
+                        atomicAdd(&wacc[wid][kk][0], hi);
+                        atomicAdd(&wacc[wid][kk][1], lo);
                     }
                 }
             }
@@ -421,16 +430,33 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
             __syncwarp();
         } else if (MODE == WALK_LITERAL_D) {
             if (lane < nbuf) {
-                int kk = bitlen32(bcode) - 1;
-                double w = (double)bcnt * kw[kk];
-                if (w > 0.0) {
-                    double lc = bcnt < 4096u ? __ldg(a.tab_log2 + bcnt) : log2((double)bcnt);
-                    accD += w * (lc + lkw[kk] - lb[kk] - L[bcode]);
+                const int k2 = bitlen32(bcode) - 1;
+                const double w = (double)bcnt * kw[k2];
+                if (w > 0.0) accD += w * L[bcode];
+                unsigned long long hi, lo;
+                clog2c_parts(bcnt, a.tabfix, hi, lo);
+                if (hi | lo) {
+                    atomicAdd(&wacc[wid][k2][0], hi);
+                    atomicAdd(&wacc[wid][k2][1], lo);
                 }
             }
+            __syncwarp();
+            // lane k: kw_k S_k - b_k log2 C(n,k) (S_k from the exact sums)
+            double term = 0.0;
+            if (lane <= n) {
+                const unsigned long long hi = wacc[wid][lane][0], lo = wacc[wid][lane][1];
+                const unsigned long long rest = ((hi & 0xffffffull) << 38) + lo;
+                const double Sk = (double)((long long)(hi >> 24) + (long long)(rest >> 62)) +
+                                  (double)(rest & (FRAC_ONE - 1ull)) * (1.0 / FRAC_SCALE);
+                wacc[wid][lane][0] = 0ull;
+                wacc[wid][lane][1] = 0ull;
+                if (kw[lane] > 0.0) term = kw[lane] * Sk - a.bk[z * (n + 1) + lane] * a.l2c[z * (n + 1) + lane];
+            }
+            __syncwarp();
+            double Dv = term - accD;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) accD += __shfl_xor_sync(FULL, accD, o);
-            if (lane == 0) a.Dout[(size_t)z * a.count + item] = accD;
+            for (int o = 16; o > 0; o >>= 1) Dv += __shfl_xor_sync(FULL, Dv, o);
+            if (lane == 0) a.Dout[(size_t)z * a.count + item] = Dv;
         }
     }
 }
@@ -684,6 +710,9 @@ bdc_status launch_literal_D(bdc_engine *e) {
     a.kw = e->bk + (size_t)e->nd * (e->n + 1);
     a.lkw = e->bk + (size_t)2 * e->nd * (e->n + 1);
     a.lb = e->bk + (size_t)3 * e->nd * (e->n + 1);
+    a.bk = e->bk;
+    a.l2c = e->bk + (size_t)5 * e->nd * (e->n + 1);
+    a.tabfix = e->tab_fix;
     a.Dout = e->lit_D;
     a.inst = e->inst;
     BDC_CUDA_TRY(cudaMemsetAsync(e->counter + 64, 0, e->nd * sizeof(uint32_t), e->stream));
