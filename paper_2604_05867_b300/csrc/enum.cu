@@ -222,6 +222,16 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int n = a.n;
     const int z = blockIdx.y;  // instance (literal D)
+    // the string z of code lane + 2 handled by this lane in closed-form subtrees:
+    // its length zm and, per symbol b, the bits j (1..zm) with z_j = b
+    static_assert(RZ == 4, "the lane-to-string map covers lengths 1..4");
+    const uint32_t zc = (uint32_t)lane + 2u;
+    const int zm = bitlen32(zc) - 1;
+    uint32_t zmatch0 = 0u, zmatch1 = 0u;
+    for (int j = 1; j <= zm && j <= RZ; j++) {
+        if ((zc >> (zm - j)) & 1u) zmatch1 |= 1u << j;
+        else zmatch0 |= 1u << j;
+    }
     const unsigned FULL = 0xffffffffu;
     if (MODE == WALK_LITERAL_D && a.inst[z * INST_STRIDE + I_ACTIVE] == 0.0) return;
     const double *L = (MODE == WALK_LITERAL_D) ? a.L + ((size_t)z << (n + 1)) : nullptr;
@@ -326,8 +336,6 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
                 Ew[j] = __shfl_sync(FULL, Eb, pm + j < 31 ? pm + j : 31);
                 xw[j] = (pm + j < n) ? (int)((x >> (n - 1 - (pm + j))) & 1u) : 2;
             }
-            const uint32_t zc = (uint32_t)lane + 2u;
-            const int m = bitlen32(zc) - 1;
             uint32_t c[RZ + 1];
             c[0] = Ew[0];
 #pragma unroll
@@ -335,25 +343,26 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
 #pragma unroll
             for (int t = 1; t <= RZ; t++) {
                 if (t <= r) {
+                    const uint32_t mt = xw[t] ? zmatch1 : zmatch0;
 #pragma unroll
-                    for (int j = RZ; j >= 1; j--)
-                        if (j <= m && (int)((zc >> (m - j)) & 1u) == xw[t]) c[j] += c[j - 1];
+                    for (int j = RZ; j >= 1; j--) c[j] += c[j - 1] * ((mt >> j) & 1u);
                     c[0] += Ew[t];
                 }
             }
             uint32_t cnt = c[1];
 #pragma unroll
             for (int j = 2; j <= RZ; j++)
-                if (m == j) cnt = c[j];
-            const bool valid = lane < 30 && m <= r && cnt > 0u;
-            const uint32_t dcode = (ccode << m) | (zc - (1u << m));
-            const int kk = kc + m;
+                if (zm == j) cnt = c[j];
+            const bool valid = lane < 30 && zm <= r && cnt > 0u;
+            const uint32_t dcode = (ccode << zm) | (zc - (1u << zm));
+            const int kk = kc + zm;
             if (MODE == WALK_STATS) {
-#pragma unroll
-                for (int mm = 1; mm <= RZ; mm++) {
-                    const int num = __popc(__ballot_sync(FULL, valid && m == mm));
-                    if (lane == kc + mm) accN += (uint32_t)num;
-                }
+                // lanes 0-1 hold the strings of length 1, 2-5 length 2, 6-13 length 3, 14-29 length 4
+                const uint32_t bal = __ballot_sync(FULL, valid);
+                if (lane == kc + 1) accN += (uint32_t)__popc(bal & 0x3u);
+                if (lane == kc + 2) accN += (uint32_t)__popc(bal & 0x3Cu);
+                if (lane == kc + 3) accN += (uint32_t)__popc(bal & 0x3FC0u);
+                if (lane == kc + 4) accN += (uint32_t)__popc(bal & 0x3FFFC000u);
                 if (valid) {
                     unsigned long long hi, lo;
                     clog2c_parts(cnt, a.tabfix, hi, lo);
