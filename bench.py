@@ -642,7 +642,8 @@ def run_config(args):
             # n=26, 7 values of d, 300 FP32 iterations each, FP64 certificate of C_26(d)/(26(1-d))
             from paper_2604_05867_b300.inputs import LARGE_SWEEP_D
             n, T = args.n or 26, args.iters or 300
-            ds = shard.shard_grid({n: list(LARGE_SWEEP_D)}, rank, world).get(n, [])
+            dlist = list(LARGE_SWEEP_D)[:args.nd] if args.nd else list(LARGE_SWEEP_D)
+            ds = shard.shard_grid({n: dlist}, rank, world).get(n, [])
             mine = {"d": ds}
             if ds:
                 t0 = time.perf_counter()
@@ -768,7 +769,8 @@ def main():
                     choices=["ba10", "n20", "batched", "dual", "large", "literal", "fp64sweep", "exact"],
                     help="run one workload configuration end to end instead of the headline bench")
     ap.add_argument("--iters", type=int, default=0)
-    ap.add_argument("--n", type=int, default=0, help="input length of the literal / fp64sweep / exact configs")
+    ap.add_argument("--n", type=int, default=0, help="input length of the literal / fp64sweep / exact / large configs")
+    ap.add_argument("--nd", type=int, default=0, help="large config: use the first ND values of its d list")
     ap.add_argument("--sched-fp32", default=None, metavar="N2,W",
                     help="use this FP32 sweep schedule (n2, column width) instead of the autotuner's")
     ap.add_argument("--sched-cache", default=None,

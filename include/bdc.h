@@ -42,7 +42,9 @@ typedef enum {
     BDC_ECUDA = -3,       /* a CUDA runtime call or kernel launch failed */
     BDC_ETIMEOUT = -4,    /* a bounded device wait gave up */
     BDC_ENONFINITE = -5,  /* a NaN/Inf reached a reduction */
-    BDC_ENOTBOUND = -6    /* no workspace bound yet */
+    BDC_ENOTBOUND = -6,   /* no workspace bound yet */
+    BDC_ECHECK = -7       /* an index check of the checked build (compiled with -DBDC_CHECKS) failed: the
+                             kernel recorded it in the instance status and skipped the access */
 } bdc_status;
 
 enum { BDC_FP32 = 0, BDC_FP64 = 1 };       /* precision of the iteration */

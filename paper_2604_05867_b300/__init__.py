@@ -19,7 +19,8 @@ from typing import Optional, Sequence
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libbdc.so")
+# BDC_CHECKED=1 loads the checked build (device-side index checks, BDC_ECHECK)
+LIB_PATH = os.path.join(_HERE, "libbdc_checks.so" if os.environ.get("BDC_CHECKED") == "1" else "libbdc.so")
 
 FP32, FP64 = 0, 1
 SWEEP, LITERAL = 0, 1
@@ -27,7 +28,7 @@ _PREC = {"fp32": FP32, "fp64": FP64, FP32: FP32, FP64: FP64}
 _IMPL = {"sweep": SWEEP, "literal": LITERAL, SWEEP: SWEEP, LITERAL: LITERAL}
 
 STATUS = {0: "BDC_OK", -1: "BDC_EINVAL", -2: "BDC_ENOMEM", -3: "BDC_ECUDA", -4: "BDC_ETIMEOUT",
-          -5: "BDC_ENONFINITE", -6: "BDC_ENOTBOUND"}
+          -5: "BDC_ENONFINITE", -6: "BDC_ENOTBOUND", -7: "BDC_ECHECK"}
 
 
 class BdcError(RuntimeError):

@@ -237,6 +237,22 @@ inline void stage_mark(bdc_engine *e, const char *name) {
     }
 }
 
+// Index checks of the checked build (compiled with -DBDC_CHECKS): a kernel
+// tests an index against the extent of the array it addresses; a failing test
+// records BDC_ECHECK in the instance status and the access is skipped, so the
+// host reads the failure after the call instead of a fault.  The release build
+// compiles the tests away.
+#ifdef BDC_CHECKS
+__device__ __forceinline__ bool bdc_in_range(size_t i, size_t extent, const double *inst_z) {
+    if (i < extent) return true;
+    if (inst_z) const_cast<double *>(inst_z)[I_STATUS] = (double)BDC_ECHECK;  // (no record without an engine)
+    return false;
+}
+#define BDC_IN_RANGE(i, extent, inst_z) bdc_in_range((size_t)(i), (size_t)(extent), (inst_z))
+#else
+#define BDC_IN_RANGE(i, extent, inst_z) true
+#endif
+
 // modes of the sweep epilogues
 enum { MODE_ITER = 0, MODE_CERT = 1, MODE_DIV = 2, MODE_DUAL = 3, MODE_DUAL_D = 4 };
 

@@ -516,6 +516,14 @@ extern "C" bdc_status bdc_bind(bdc_engine *e, void *ws, size_t bytes, void *stre
     BDC_TRY(sweep_prepare<float>(e, e->f32));
     BDC_TRY(sweep_prepare<double>(e, e->f64));
     BDC_TRY(sync_check(e, "bdc_bind precompute"));
+    {
+        // a status recorded by the precompute (the checked build's index checks)
+        std::vector<double> h;
+        BDC_TRY(read_inst(e, h));
+        for (int z = 0; z < nd; z++)
+            if (h[(size_t)z * INST_STRIDE + I_STATUS] != 0.0)
+                BDC_FAIL((bdc_status)(int)h[(size_t)z * INST_STRIDE + I_STATUS], "bdc_bind: the precompute recorded a failure");
+    }
     e->cur = 0;
     e->bound = true;
     return BDC_OK;
@@ -785,6 +793,7 @@ extern "C" bdc_status bdc_ba_iterate(bdc_engine *e, int max_iters, double tol, i
     }
     e->iters_total += done;
     if (st == BDC_ETIMEOUT) bdc_set_error("bdc_ba_iterate: a bounded device wait gave up (instance stopped)");
+    else if (st == BDC_ECHECK) bdc_set_error("bdc_ba_iterate: an index check of the checked build failed (instance stopped)");
     else if (st != BDC_OK) bdc_set_error("bdc_ba_iterate: non-finite value in a reduction (instance stopped)");
     return st;
 }

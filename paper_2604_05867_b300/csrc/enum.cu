@@ -234,6 +234,8 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
     }
     const unsigned FULL = 0xffffffffu;
     if (MODE == WALK_LITERAL_D && a.inst[z * INST_STRIDE + I_ACTIVE] == 0.0) return;
+    const double *st_z = a.inst ? a.inst + z * INST_STRIDE : nullptr;  // where index checks record
+    (void)st_z;
     const double *L = (MODE == WALK_LITERAL_D) ? a.L + ((size_t)z << (n + 1)) : nullptr;
     const double *kw = (MODE == WALK_LITERAL_D) ? a.kw + z * (n + 1) : nullptr;
     if (MODE != WALK_EMIT && lane <= BDC_MAXN) {
@@ -278,7 +280,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
             uint32_t E = (xb == b) ? 1u : 0u;
             uint32_t c = __popc(__ballot_sync(FULL, xb == b));
             if (c > 0) {
-                stkE[wid][sp][lane] = E;
+                if (BDC_IN_RANGE(sp, STK, st_z)) stkE[wid][sp][lane] = E;
                 if (lane == sp) { stk_code = 2u | (uint32_t)b; stk_cnt = c; }
                 sp++;
             }
@@ -298,7 +300,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
                     nbuf = 0;
                 }
             } else if (MODE == WALK_EMIT) {
-                if (lane == 0) a.emb[code] = cnt;
+                if (lane == 0 && BDC_IN_RANGE(code, (size_t)2 << n, st_z)) a.emb[code] = cnt;
             } else {
                 // D_x = sum_k [kw_k S_k(x) - b_k log2 C(n,k)] - sum_y kw_|y| Count(y,x) L(y):
                 // per node the cross term in FP64 and count*log2(count) in exact
@@ -308,7 +310,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
                 if (nbuf == 32) {
                     const int k2 = bitlen32(bcode) - 1;
                     const double w = (double)bcnt * kw[k2];
-                    if (w > 0.0) accD += w * L[bcode];
+                    if (w > 0.0 && BDC_IN_RANGE(bcode, (size_t)2 << n, st_z)) accD += w * L[bcode];
                     unsigned long long hi, lo;
                     clog2c_parts(bcnt, a.tabfix, hi, lo);
                     if (hi | lo) {
@@ -372,11 +374,11 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
                     }
                 }
             } else if (MODE == WALK_EMIT) {
-                if (valid) a.emb[dcode] = cnt;
+                if (valid && BDC_IN_RANGE(dcode, (size_t)2 << n, st_z)) a.emb[dcode] = cnt;
             } else {
                 if (valid) {
                     const double w = (double)cnt * kw[kk];
-                    if (w > 0.0) accD += w * L[dcode];
+                    if (w > 0.0 && BDC_IN_RANGE(dcode, (size_t)2 << n, st_z)) accD += w * L[dcode];
                     unsigned long long hi, lo;
                     clog2c_parts(cnt, a.tabfix, hi, lo);
                     if (hi | lo) {
@@ -407,7 +409,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
                         record((code << 1) | (uint32_t)b, k + 1, cb);
                         subtree((code << 1) | (uint32_t)b, k + 1, Eb, pm);
                     } else {
-                        stkE[wid][sp][lane] = Eb;
+                        if (BDC_IN_RANGE(sp, STK, st_z)) stkE[wid][sp][lane] = Eb;
                         if (lane == sp) { stk_code = (code << 1) | (uint32_t)b; stk_cnt = cb; }
                         sp++;
                     }
@@ -432,16 +434,17 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
                 accF = rest & (FRAC_ONE - 1ull);
                 wacc[wid][lane][0] = 0ull;
                 wacc[wid][lane][1] = 0ull;
-                if (a.Nk32) a.Nk32[item * a.stride + lane] = accN;
-                if (a.Nk64) a.Nk64[item * a.stride + lane] = accN;
-                if (a.Sk) a.Sk[item * a.stride + lane] = (double)accI + (double)accF * (1.0 / FRAC_SCALE);
+                const bool ok = BDC_IN_RANGE(item, a.count, st_z);
+                if (ok && a.Nk32) a.Nk32[item * a.stride + lane] = accN;
+                if (ok && a.Nk64) a.Nk64[item * a.stride + lane] = accN;
+                if (ok && a.Sk) a.Sk[item * a.stride + lane] = (double)accI + (double)accF * (1.0 / FRAC_SCALE);
             }
             __syncwarp();
         } else if (MODE == WALK_LITERAL_D) {
             if (lane < nbuf) {
                 const int k2 = bitlen32(bcode) - 1;
                 const double w = (double)bcnt * kw[k2];
-                if (w > 0.0) accD += w * L[bcode];
+                if (w > 0.0 && BDC_IN_RANGE(bcode, (size_t)2 << n, st_z)) accD += w * L[bcode];
                 unsigned long long hi, lo;
                 clog2c_parts(bcnt, a.tabfix, hi, lo);
                 if (hi | lo) {
@@ -465,7 +468,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
             double Dv = term - accD;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) Dv += __shfl_xor_sync(FULL, Dv, o);
-            if (lane == 0) a.Dout[(size_t)z * a.count + item] = Dv;
+            if (lane == 0 && BDC_IN_RANGE(item, a.count, st_z)) a.Dout[(size_t)z * a.count + item] = Dv;
         }
     }
 }
@@ -499,6 +502,8 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_super_walk(SuperArgs a, 
     const int n = a.n;
     const int z = blockIdx.y;
     if (a.inst[z * INST_STRIDE + I_ACTIVE] == 0.0) return;
+    const double *inst_z = a.inst + z * INST_STRIDE;  // where index checks record
+    (void)inst_z;
     const double *p = a.p + ((size_t)z << n);
     while (true) {
         uint32_t v = 0;
@@ -561,7 +566,8 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_super_walk(SuperArgs a, 
                     }
                 }
                 const uint32_t cnt = w[RB];
-                if (lane < (1 << r) && cnt) acc += p[((size_t)xpre << r) | (uint32_t)lane] * (double)cnt;
+                const size_t xi = ((size_t)xpre << r) | (uint32_t)lane;
+                if (lane < (1 << r) && cnt && BDC_IN_RANGE(xi, (size_t)1 << n, inst_z)) acc += p[xi] * (double)cnt;
             };
             if (dstop == s) {
                 leaves(M, prefix, n - s);
@@ -573,7 +579,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_super_walk(SuperArgs a, 
                 int depth = s;
                 uint32_t x = prefix;
                 uint32_t nb_lane = 0;
-                stkM[wid][depth][lane] = M;
+                if (BDC_IN_RANGE(depth, STK, inst_z)) stkM[wid][depth][lane] = M;
                 while (true) {
                     int b = (int)__shfl_sync(FULL, nb_lane, depth);
                     if (b > 1) {
@@ -596,14 +602,14 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_super_walk(SuperArgs a, 
                     depth++;
                     x = (x << 1) | (uint32_t)b;
                     M = Mc;
-                    stkM[wid][depth][lane] = M;
+                    if (BDC_IN_RANGE(depth, STK, inst_z)) stkM[wid][depth][lane] = M;
                     if (lane == depth) nb_lane = 0;
                 }
             }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
-        if (lane == 0) a.part[(size_t)z * a.nitems + item] = acc;
+        if (lane == 0 && BDC_IN_RANGE(item, a.nitems, inst_z)) a.part[(size_t)z * a.nitems + item] = acc;
     }
 }
 
@@ -701,6 +707,7 @@ bdc_status launch_subseq_stats(bdc_engine *e) {
     a.Sk = e->Sk;
     a.stride = e->n + 1;
     a.tabfix = e->tab_fix;
+    a.inst = e->inst;  // (instance 0's status receives index-check failures of the checked build)
     BDC_CUDA_TRY(cudaMemsetAsync(e->counter, 0, 64 * sizeof(uint32_t), e->stream));
     k_subseq_walk<WALK_STATS><<<walk_grid(), WARPS_PER_CTA * 32, 0, e->stream>>>(a); e->launches++;
     BDC_CUDA_TRY(cudaGetLastError());

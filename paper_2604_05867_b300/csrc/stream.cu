@@ -43,6 +43,7 @@ __global__ void k_stream_init_fwd(int n, T *p, const T *D, T *A, double *part, i
     const T sh = (T)I[I_SHIFT];
     double s = 0.0;
     for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < M; c += (size_t)gridDim.x * blockDim.x) {
+        if (!BDC_IN_RANGE(c, M, I)) continue;
         if (c < N) {
             Az[c] = (T)0;
         } else {
@@ -82,9 +83,11 @@ __global__ void k_stream_fwd(int n, int i, const T *__restrict__ A, T *__restric
             const int k = 63 - __clzll((long long)cu);  // |u|
             if (k <= i) {
                 const size_t base = (cu << (rest + 1)) | s;
-                v = Az[base] + Az[base | ((size_t)1 << rest)];
+                if (BDC_IN_RANGE(base | ((size_t)1 << rest), M, inst + z * INST_STRIDE))
+                    v = Az[base] + Az[base | ((size_t)1 << rest)];
             }
-            if (k >= 1) v = v + Az[((cu >> 1) << (rest + 1)) | ((cu & 1u) << rest) | s];
+            const size_t j = ((cu >> 1) << (rest + 1)) | ((cu & 1u) << rest) | s;
+            if (k >= 1 && BDC_IN_RANGE(j, M, inst + z * INST_STRIDE)) v = v + Az[j];
         }
         Bz[P] = v;
     }
@@ -140,8 +143,10 @@ __global__ void k_stream_adj(int n, int i, const T *__restrict__ A, T *__restric
     for (size_t P = (size_t)blockIdx.x * blockDim.x + threadIdx.x; P < M; P += (size_t)gridDim.x * blockDim.x) {
         const size_t cv = P >> (rest + 1), b = (P >> rest) & 1u, s = P & smask;
         T v = (T)0;
-        if (cv != 0 && cv < ((size_t)2 << i))
-            v = Az[(cv << rest) | s] + Az[(((cv << 1) | b) << rest) | s];
+        const size_t j1 = (cv << rest) | s, j2 = (((cv << 1) | b) << rest) | s;
+        if (cv != 0 && cv < ((size_t)2 << i) && BDC_IN_RANGE(j1, M, inst + z * INST_STRIDE) &&
+            BDC_IN_RANGE(j2, M, inst + z * INST_STRIDE))
+            v = Az[j1] + Az[j2];
         Bz[P] = v;
     }
 }

@@ -1066,7 +1066,8 @@ __global__ void __launch_bounds__(256) k_combine_k(SweepArgs a, const T *__restr
                 // the term of code y0 + t is src[+-t] for one base per CTA
                 const uint32_t u20 = y0 & ((1u << l) - 1u);
                 uint32_t c1 = (1u << j) | (y0 >> l);
-                const T *src;
+                const T *src, *arr;
+                size_t ext;
                 int sgn = 1;
                 if (l == n2) {
                     uint32_t u2b = u20;
@@ -1075,12 +1076,21 @@ __global__ void __launch_bounds__(256) k_combine_k(SweepArgs a, const T *__restr
                         u2b = full2 - u20;
                         sgn = -1;
                     }
+                    arr = (j == n1) ? pz : Fz;
+                    ext = a.strideN;
                     src = ((j == n1) ? pz + ((size_t)(c1 ^ (1u << n1)) << n2) : Fz + ((size_t)c1 << n2)) + u2b;
                 } else {
+                    arr = Tmz;
+                    ext = a.strideM;
                     src = Tmz + ((size_t)c1 << n2) + (1u << l) + u20;
                 }
+                (void)arr;
+                (void)ext;
 #pragma unroll
-                for (int r = 0; r < RC; r++) acc[r] += src[sgn * (int)(r * 256 + threadIdx.x)];
+                for (int r = 0; r < RC; r++) {
+                    const int off = sgn * (int)(r * 256 + threadIdx.x);
+                    if (BDC_IN_RANGE((src - arr) + off, ext, a.inst + z * INST_STRIDE)) acc[r] += src[off];
+                }
                 continue;
             }
 #pragma unroll
@@ -1089,17 +1099,22 @@ __global__ void __launch_bounds__(256) k_combine_k(SweepArgs a, const T *__restr
                 if (y >= cnt) break;
                 uint32_t c1 = (1u << j) | (y >> l);
                 uint32_t u2 = y & ((1u << l) - 1u);
-                T v;
+                T v = (T)0;
+                const double *st = a.inst + z * INST_STRIDE;
+                (void)st;
                 if (l == n2) {
                     if (HALF && u2 >= hh) {  // complement column of the complement row
                         c1 = c1 ^ ((1u << j) - 1u);
                         u2 = full2 - u2;
                     }
-                    v = (j == n1) ? pz[((size_t)(c1 ^ (1u << n1)) << n2) | u2] : Fz[((size_t)c1 << n2) | u2];
+                    const size_t ip = ((size_t)(c1 ^ (1u << n1)) << n2) | u2, ifl = ((size_t)c1 << n2) | u2;
+                    if (BDC_IN_RANGE(j == n1 ? ip : ifl, a.strideN, st)) v = (j == n1) ? pz[ip] : Fz[ifl];
                 } else if (l < 5) {
-                    v = Tsz[((size_t)((1u << l) | u2) << (n1 + 1)) + c1];
+                    const size_t is = ((size_t)((1u << l) | u2) << (n1 + 1)) + c1;
+                    if (BDC_IN_RANGE(is, (size_t)32 << (n1 + 1), st)) v = Tsz[is];
                 } else {
-                    v = Tmz[((size_t)c1 << n2) + ((1u << l) | u2)];
+                    const size_t im = ((size_t)c1 << n2) + ((1u << l) | u2);
+                    if (BDC_IN_RANGE(im, a.strideM, st)) v = Tmz[im];
                 }
                 acc[r] += v;
             }

@@ -88,3 +88,12 @@ def test_schedules_up_to_n28(n):
         assert n2.value == -1
     assert L.bdc_workspace_bytes(h) < 200e9
     L.bdc_destroy(h)
+
+
+def test_checked_build_exports_every_declared_symbol():
+    from paper_2604_05867_b300 import build
+    if not os.path.exists(build.LIB_CHECKS):
+        pytest.skip("checked build not compiled")
+    L = ctypes.CDLL(build.LIB_CHECKS)
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
