@@ -258,6 +258,26 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
         if (item >= a.count) break;
         uint64_t x = a.xs32 ? (uint64_t)a.xs32[item] : a.xs64[item];
         const int xb = (lane < n) ? (int)((x >> (n - 1 - lane)) & 1u) : 2;
+        // Az[t] = Count(z, x[i+1:]) at window position i = n - 1 - RZ + t for this
+        // lane's string z, by the suffix DP Cs[j] = #embeddings of z_j..z_zm in
+        // the suffix read so far (Cs[zm+1] = 1), prepending x_i: Cs[j] += [z_j = x_i] Cs[j+1]
+        uint32_t Az[RZ + 1];
+        {
+            uint32_t Cs[RZ + 2];
+#pragma unroll
+            for (int j = 1; j <= RZ + 1; j++) Cs[j] = (j == zm + 1) ? 1u : 0u;
+            Cs[0] = 0u;
+#pragma unroll
+            for (int t = RZ; t >= 0; t--) {
+                const int i = n - 1 - RZ + t;
+                Az[t] = Cs[1];
+                if (i >= 0) {
+                    const uint32_t mt = ((x >> (n - 1 - i)) & 1u) ? zmatch1 : zmatch0;
+#pragma unroll
+                    for (int j = 1; j <= RZ; j++) Cs[j] += ((mt >> j) & 1u) * Cs[j + 1];
+                }
+            }
+        }
         // per-lane accumulators: lane k owns length k (stats) / a 32-slot
         // gather buffer (literal D)
         uint32_t accN = (lane == 0) ? 1u : 0u;
@@ -322,40 +342,23 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
             }
         };
         // The whole subtree below a child y' whose embeddings all end at or after
-        // position pm, r = n - 1 - pm <= RZ, in closed form, one descendant per
-        // lane: lane l stands for the string z of code l + 2 (every string of
-        // length 1..RZ in lanes 0..29) and runs the embedding DP of y' z over the
-        // last r positions, from c_0 = the embeddings of y' ending before the
-        // position (a prefix sum of E) and c_j = 0 (z_1 must come after y' ends):
-        // c_j += [x_t = z_j] c_{j-1}.  Count(y' z, x) = c_m; distinct lanes are
-        // distinct strings, and a count of 0 means z does not follow y' in x.
-        auto subtree = [&](uint32_t ccode, int kc, uint32_t Eb, int pm) {
-            const int r = n - 1 - pm;
-            uint32_t Ew[RZ + 1];
-            int xw[RZ + 1];
+        // position pm, n - 1 - pm <= RZ, in closed form, one descendant per lane:
+        // lane l stands for the string z of code l + 2 (every string of length
+        // 1..RZ in lanes 0..29); its count Count(y' z, x) = sum_i E[i] Count(z, x[i+1:])
+        // is linear in the embedding-end vector E, with the coefficients Az of the
+        // lane's z taken once per input; distinct lanes are distinct strings, and a
+        // count of 0 means z does not follow y' in x.
+        auto subtree = [&](uint32_t ccode, int kc, uint32_t Eb) {
+            // Count(y' z, x) = sum_i E[i] Count(z, x[i+1:]); E vanishes below the
+            // window, and Az holds the second factor at every window position
+            uint32_t cnt = 0u;
 #pragma unroll
-            for (int j = 0; j <= RZ; j++) {
-                Ew[j] = __shfl_sync(FULL, Eb, pm + j < 31 ? pm + j : 31);
-                xw[j] = (pm + j < n) ? (int)((x >> (n - 1 - (pm + j))) & 1u) : 2;
+            for (int t = 0; t <= RZ; t++) {
+                const int i = n - 1 - RZ + t;
+                const uint32_t e = __shfl_sync(FULL, Eb, i >= 0 ? i : 0);
+                cnt += (i >= 0 ? e : 0u) * Az[t];
             }
-            uint32_t c[RZ + 1];
-            c[0] = Ew[0];
-#pragma unroll
-            for (int j = 1; j <= RZ; j++) c[j] = 0u;
-#pragma unroll
-            for (int t = 1; t <= RZ; t++) {
-                if (t <= r) {
-                    const uint32_t mt = xw[t] ? zmatch1 : zmatch0;
-#pragma unroll
-                    for (int j = RZ; j >= 1; j--) c[j] += c[j - 1] * ((mt >> j) & 1u);
-                    c[0] += Ew[t];
-                }
-            }
-            uint32_t cnt = c[1];
-#pragma unroll
-            for (int j = 2; j <= RZ; j++)
-                if (zm == j) cnt = c[j];
-            const bool valid = lane < 30 && zm <= r && cnt > 0u;
+            const bool valid = lane < 30 && cnt > 0u;
             const uint32_t dcode = (ccode << zm) | (zc - (1u << zm));
             const int kk = kc + zm;
             if (MODE == WALK_STATS) {
@@ -407,7 +410,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
                         // the child's subtree spans the last RZ positions at most:
                         // record it and all its descendants here instead of stacking it
                         record((code << 1) | (uint32_t)b, k + 1, cb);
-                        subtree((code << 1) | (uint32_t)b, k + 1, Eb, pm);
+                        subtree((code << 1) | (uint32_t)b, k + 1, Eb);
                     } else {
                         if (BDC_IN_RANGE(sp, STK, st_z)) stkE[wid][sp][lane] = Eb;
                         if (lane == sp) { stk_code = (code << 1) | (uint32_t)b; stk_cnt = cb; }
