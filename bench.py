@@ -87,19 +87,20 @@ def kernel_source_hash() -> str:
 
 
 def measured_counters(stage: str, n: int, sched: dict):
-    """(dram_bytes, smem_wavefronts, source) of one launch of `stage`, or
-    (None, None, why) when no capture of the current kernels exists."""
+    """(counters, source) of one launch of `stage`: the capture's record
+    (dram_bytes, smem_wavefronts, lsu_wavefronts, ...), or ({}, why) when no
+    capture of the current kernels exists."""
     try:
         with open(COUNTERS) as f:
             j = json.load(f)
     except Exception:
-        return None, None, "no counter file"
+        return {}, "no counter file"
     if j.get("source_sha") != kernel_source_hash():
-        return None, None, "kernels changed since the capture"
+        return {}, "kernels changed since the capture"
     for r in j.get("launches", []):
         if (r["stage"], r["n"], r["n1"], r["n2"], r["width"]) == (stage, n, sched["n1"], sched["n2"], sched["width"]):
-            return r.get("dram_bytes"), r.get("smem_wavefronts"), j.get("command", "")
-    return None, None, "no capture of this schedule"
+            return r, j.get("command", "")
+    return {}, "no capture of this schedule"
 
 
 # ----------------------------------------------------------------------------
@@ -295,7 +296,15 @@ def run_ours(args, rank: int, world: int):
         gpu_id = str(gpu_id) if gpu_id else str(local)
         clocks = ClockSampler(gpu_id)
         clocks.start()
-        time.sleep(0.5)
+        # keep the GPU under load (untimed iterations) while the sampler starts:
+        # after half a second idle the first kernels run measurably slower (the
+        # forward rows pass by up to 20% for a while), so the timed steps follow
+        # load, not an idle gap; then the W warm-up steps again
+        t_load = time.perf_counter()
+        while time.perf_counter() - t_load < 0.5:
+            eng.iterate(chunk, -1.0, "fp32", "sweep")
+            torch.cuda.synchronize()
+        eng.iterate(args.warmup, -1.0, "fp32", "sweep")
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
@@ -310,6 +319,9 @@ def run_ours(args, rank: int, world: int):
             dist.barrier()
         ms_total = ev0.elapsed_time(ev1)
         launches = eng.launch_count() - launches0
+        # per-stage times (events after every kernel, no graph), same workload,
+        # taken straight after the timed steps while the GPU is still under load
+        stages = eng.profile("fp32", "sweep", reps=5) if rank == 0 else None
         clk = clocks.stop()
         ms = shard.max_over_ranks(ms_total / args.steps, device=dev)  # slowest rank's time per step
         # every rank iterates its own instance: the job covers `world` instances per step
@@ -317,15 +329,14 @@ def run_ours(args, rank: int, world: int):
 
         extra = {}
         if rank == 0:
-            # per-stage times (events after every kernel, no graph), same workload
-            stages = eng.profile("fp32", "sweep", reps=5)
             half = sched32["n2"] > 0 and sched32["width"] < (1 << sched32["n2"])
             sb = stage_bytes(n, sched32["n1"], sched32["n2"], 4, half)
             peaks = measured_peaks()
             dev_peaks = bdc.measure_peaks(stream)
             top = max((k for k in stages if k in sb and sb[k] > 0), key=lambda k: stages[k])
             achieved = sb[top] / (stages[top] / 1000.0) / 1e9
-            dram, wf, csrc = measured_counters(top, n, sched32)
+            cnt, csrc = measured_counters(top, n, sched32)
+            dram, wf, lsu = cnt.get("dram_bytes"), cnt.get("smem_wavefronts"), cnt.get("lsu_wavefronts")
             roof = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved / peaks["hbm_gbs"], "traffic": dram,
                     "peak_source": peaks["source"], "algorithmic_bytes": sb[top],
@@ -339,6 +350,17 @@ def run_ours(args, rank: int, world: int):
                                          "frac": smem_tb / dev_peaks["smem_tbs"],
                                          "source": "ncu shared-memory wavefronts of one launch x 128 B / this run's "
                                                    "event time; peak measured in this run"}
+            if lsu is not None and clk.get("sm_mhz"):
+                # the L1 data pipe that serves both the shared-memory steps and
+                # the 16-byte global accesses of 4-column tile rows: one
+                # wavefront per cycle per SM at the SM clock sampled in this run
+                lsu_rate = lsu / (stages[top] / 1000.0) / 1e9
+                lsu_peak = dev_peaks["sms"] * clk["sm_mhz"] / 1e3
+                roof["l1_data_pipe"] = {"wavefronts_per_launch": lsu, "shared_wavefronts": wf,
+                                        "achieved": lsu_rate, "peak": lsu_peak, "unit": "G wavefronts/s",
+                                        "frac": lsu_rate / lsu_peak,
+                                        "source": "ncu l1tex__data_pipe_lsu_wavefronts.sum of one launch / this "
+                                                  "run's event time; peak 1 wavefront/cycle/SM x SMs x sampled SM clock"}
             stage_total = sum(stages.values())
 
             # FP64 sweep iteration (same-algorithm precision baseline)

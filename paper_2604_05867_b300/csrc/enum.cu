@@ -311,8 +311,8 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
                 if (lane == kk) accN++;
                 if (lane == nbuf) { bcode = (uint32_t)kk; bcnt = cnt; }
                 if (++nbuf == 32) {
-                    unsigned long long hi, lo;
-                    clog2c_parts(bcnt, a.tabfix, hi, lo);
+                    unsigned long long hi = 0ull, lo = 0ull;
+                    if (bcnt > 1u) clog2c_parts(bcnt, a.tabfix, hi, lo);
                     if (hi | lo) {
                         atomicAdd(&wacc[wid][bcode][0], hi);
                         atomicAdd(&wacc[wid][bcode][1], lo);
@@ -331,8 +331,8 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
                     const int k2 = bitlen32(bcode) - 1;
                     const double w = (double)bcnt * kw[k2];
                     if (w > 0.0 && BDC_IN_RANGE(bcode, (size_t)2 << n, st_z)) accD += w * L[bcode];
-                    unsigned long long hi, lo;
-                    clog2c_parts(bcnt, a.tabfix, hi, lo);
+                    unsigned long long hi = 0ull, lo = 0ull;
+                    if (bcnt > 1u) clog2c_parts(bcnt, a.tabfix, hi, lo);
                     if (hi | lo) {
                         atomicAdd(&wacc[wid][k2][0], hi);
                         atomicAdd(&wacc[wid][k2][1], lo);
@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
                 if (lane == kc + 2) accN += (uint32_t)__popc(bal & 0x3Cu);
                 if (lane == kc + 3) accN += (uint32_t)__popc(bal & 0x3FC0u);
                 if (lane == kc + 4) accN += (uint32_t)__popc(bal & 0x3FFFC000u);
-                if (valid) {
+                if (valid && cnt > 1u) {  // (a count of 1 adds 1 log2 1 = 0)
                     unsigned long long hi, lo;
                     clog2c_parts(cnt, a.tabfix, hi, lo);
                     if (hi | lo) {
@@ -382,8 +382,8 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
                 if (valid) {
                     const double w = (double)cnt * kw[kk];
                     if (w > 0.0 && BDC_IN_RANGE(dcode, (size_t)2 << n, st_z)) accD += w * L[dcode];
-                    unsigned long long hi, lo;
-                    clog2c_parts(cnt, a.tabfix, hi, lo);
+                    unsigned long long hi = 0ull, lo = 0ull;
+                    if (cnt > 1u) clog2c_parts(cnt, a.tabfix, hi, lo);
                     if (hi | lo) {
                         atomicAdd(&wacc[wid][kk][0], hi);
                         atomicAdd(&wacc[wid][kk][1], lo);
@@ -421,8 +421,8 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
         }
         if (MODE == WALK_STATS) {
             if (lane < nbuf) {
-                unsigned long long hi, lo;
-                clog2c_parts(bcnt, a.tabfix, hi, lo);
+                unsigned long long hi = 0ull, lo = 0ull;
+                if (bcnt > 1u) clog2c_parts(bcnt, a.tabfix, hi, lo);
                 if (hi | lo) {
                     atomicAdd(&wacc[wid][bcode][0], hi);
                     atomicAdd(&wacc[wid][bcode][1], lo);
@@ -448,8 +448,8 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
                 const int k2 = bitlen32(bcode) - 1;
                 const double w = (double)bcnt * kw[k2];
                 if (w > 0.0 && BDC_IN_RANGE(bcode, (size_t)2 << n, st_z)) accD += w * L[bcode];
-                unsigned long long hi, lo;
-                clog2c_parts(bcnt, a.tabfix, hi, lo);
+                unsigned long long hi = 0ull, lo = 0ull;
+                if (bcnt > 1u) clog2c_parts(bcnt, a.tabfix, hi, lo);
                 if (hi | lo) {
                     atomicAdd(&wacc[wid][k2][0], hi);
                     atomicAdd(&wacc[wid][k2][1], lo);

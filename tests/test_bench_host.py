@@ -66,6 +66,12 @@ def test_counter_file_is_consistent():
     real = bench.kernel_source_hash
     try:
         bench.kernel_source_hash = lambda: "0" * 16
-        assert bench.measured_counters(j["launches"][0]["stage"], j["launches"][0]["n"], sched)[0] is None
+        assert bench.measured_counters(j["launches"][0]["stage"], j["launches"][0]["n"], sched)[0] == {}
     finally:
         bench.kernel_source_hash = real
+    # with the current source, every record carries the L1 data-pipe total,
+    # which includes the shared-memory wavefronts
+    if j["source_sha"] == bench.kernel_source_hash():
+        for r in j["launches"]:
+            got, _ = bench.measured_counters(r["stage"], r["n"], {k: r[k] for k in ("n1", "n2", "width")})
+            assert got["lsu_wavefronts"] >= got["smem_wavefronts"] > 0
