@@ -213,7 +213,9 @@ struct WalkArgs {
 
 template <int MODE>
 __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) {
-    constexpr int RZ = 4;  // subtrees spanning at most RZ positions are done in closed form (30 strings <= 32 lanes)
+    // subtrees spanning at most RZ positions are done in closed form: the 62
+    // strings of length 1..5, two per lane
+    constexpr int RZ = 5;
     __shared__ uint32_t stkE[WARPS_PER_CTA][STK][32];
     // WALK_STATS: per warp and length, the exact sums of c*log2(c) (hi, lo parts);
     // nodes are buffered 32 at a time (lane i holds the i-th) and folded in by
@@ -222,15 +224,21 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int n = a.n;
     const int z = blockIdx.y;  // instance (literal D)
-    // the string z of code lane + 2 handled by this lane in closed-form subtrees:
-    // its length zm and, per symbol b, the bits j (1..zm) with z_j = b
-    static_assert(RZ == 4, "the lane-to-string map covers lengths 1..4");
+    // the strings handled by this lane in closed-form subtrees: z of code
+    // lane + 2 (lanes 0..29: every string of length 1..4) and z5 = the 5 bits
+    // of the lane (every string of length 5); per string its length and, per
+    // symbol b, the bits j (1..length) with z_j = b
+    static_assert(RZ == 5, "the lane-to-string map covers lengths 1..5");
     const uint32_t zc = (uint32_t)lane + 2u;
     const int zm = bitlen32(zc) - 1;
-    uint32_t zmatch0 = 0u, zmatch1 = 0u;
-    for (int j = 1; j <= zm && j <= RZ; j++) {
+    uint32_t zmatch0 = 0u, zmatch1 = 0u, z5match0 = 0u, z5match1 = 0u;
+    for (int j = 1; j <= zm && j <= 4; j++) {
         if ((zc >> (zm - j)) & 1u) zmatch1 |= 1u << j;
         else zmatch0 |= 1u << j;
+    }
+    for (int j = 1; j <= 5; j++) {
+        if (((uint32_t)lane >> (5 - j)) & 1u) z5match1 |= 1u << j;
+        else z5match0 |= 1u << j;
     }
     const unsigned FULL = 0xffffffffu;
     if (MODE == WALK_LITERAL_D && a.inst[z * INST_STRIDE + I_ACTIVE] == 0.0) return;
@@ -259,22 +267,31 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
         uint64_t x = a.xs32 ? (uint64_t)a.xs32[item] : a.xs64[item];
         const int xb = (lane < n) ? (int)((x >> (n - 1 - lane)) & 1u) : 2;
         // Az[t] = Count(z, x[i+1:]) at window position i = n - 1 - RZ + t for this
-        // lane's string z, by the suffix DP Cs[j] = #embeddings of z_j..z_zm in
-        // the suffix read so far (Cs[zm+1] = 1), prepending x_i: Cs[j] += [z_j = x_i] Cs[j+1]
-        uint32_t Az[RZ + 1];
+        // lane's string z (A5 likewise for z5), by the suffix DP Cs[j] =
+        // #embeddings of z_j..z_zm in the suffix read so far (Cs[zm+1] = 1),
+        // prepending x_i: Cs[j] += [z_j = x_i] Cs[j+1]
+        uint32_t Az[RZ + 1], A5[RZ + 1];
         {
-            uint32_t Cs[RZ + 2];
+            uint32_t Cs[RZ + 2], C5[RZ + 2];
 #pragma unroll
-            for (int j = 1; j <= RZ + 1; j++) Cs[j] = (j == zm + 1) ? 1u : 0u;
-            Cs[0] = 0u;
+            for (int j = 1; j <= RZ + 1; j++) {
+                Cs[j] = (j == zm + 1) ? 1u : 0u;
+                C5[j] = (j == 6) ? 1u : 0u;
+            }
+            Cs[0] = C5[0] = 0u;
 #pragma unroll
             for (int t = RZ; t >= 0; t--) {
                 const int i = n - 1 - RZ + t;
                 Az[t] = Cs[1];
+                A5[t] = C5[1];
                 if (i >= 0) {
-                    const uint32_t mt = ((x >> (n - 1 - i)) & 1u) ? zmatch1 : zmatch0;
+                    const bool one = (x >> (n - 1 - i)) & 1u;
+                    const uint32_t mt = one ? zmatch1 : zmatch0, m5 = one ? z5match1 : z5match0;
 #pragma unroll
-                    for (int j = 1; j <= RZ; j++) Cs[j] += ((mt >> j) & 1u) * Cs[j + 1];
+                    for (int j = 1; j <= RZ; j++) {
+                        Cs[j] += ((mt >> j) & 1u) * Cs[j + 1];
+                        C5[j] += ((m5 >> j) & 1u) * C5[j + 1];
+                    }
                 }
             }
         }
@@ -342,54 +359,65 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_subseq_walk(WalkArgs a) 
             }
         };
         // The whole subtree below a child y' whose embeddings all end at or after
-        // position pm, n - 1 - pm <= RZ, in closed form, one descendant per lane:
+        // position pm, n - 1 - pm <= RZ, in closed form, two descendants per lane:
         // lane l stands for the string z of code l + 2 (every string of length
-        // 1..RZ in lanes 0..29); its count Count(y' z, x) = sum_i E[i] Count(z, x[i+1:])
-        // is linear in the embedding-end vector E, with the coefficients Az of the
-        // lane's z taken once per input; distinct lanes are distinct strings, and a
-        // count of 0 means z does not follow y' in x.
+        // 1..4 in lanes 0..29) and for z5, its 5 bits (every string of length 5);
+        // a count Count(y' z, x) = sum_i E[i] Count(z, x[i+1:]) is linear in the
+        // embedding-end vector E, with the coefficients Az (A5) of the lane's
+        // strings taken once per input; distinct lanes are distinct strings, and
+        // a count of 0 means z does not follow y' in x.
         auto subtree = [&](uint32_t ccode, int kc, uint32_t Eb) {
-            // Count(y' z, x) = sum_i E[i] Count(z, x[i+1:]); E vanishes below the
-            // window, and Az holds the second factor at every window position
-            uint32_t cnt = 0u;
+            // E vanishes below the window, and Az / A5 hold the second factor at
+            // every window position
+            uint32_t cnt = 0u, cnt5 = 0u;
 #pragma unroll
             for (int t = 0; t <= RZ; t++) {
                 const int i = n - 1 - RZ + t;
                 const uint32_t e = __shfl_sync(FULL, Eb, i >= 0 ? i : 0);
-                cnt += (i >= 0 ? e : 0u) * Az[t];
+                if (i >= 0) {
+                    cnt += e * Az[t];
+                    cnt5 += e * A5[t];
+                }
             }
-            const bool valid = lane < 30 && cnt > 0u;
-            const uint32_t dcode = (ccode << zm) | (zc - (1u << zm));
-            const int kk = kc + zm;
+            const bool valid = lane < 30 && cnt > 0u, valid5 = cnt5 > 0u;
+            // one descendant: its code, length and count
+            auto leaf = [&](bool ok, uint32_t dcode, int kk, uint32_t c) {
+                if (MODE == WALK_STATS) {
+                    if (ok && c > 1u) {  // (a count of 1 adds 1 log2 1 = 0)
+                        unsigned long long hi, lo;
+                        clog2c_parts(c, a.tabfix, hi, lo);
+                        if (hi | lo) {
+                            atomicAdd(&wacc[wid][kk][0], hi);
+                            atomicAdd(&wacc[wid][kk][1], lo);
+                        }
+                    }
+                } else if (MODE == WALK_EMIT) {
+                    if (ok && BDC_IN_RANGE(dcode, (size_t)2 << n, st_z)) a.emb[dcode] = c;
+                } else {
+                    if (ok) {
+                        const double w = (double)c * kw[kk];
+                        if (w > 0.0 && BDC_IN_RANGE(dcode, (size_t)2 << n, st_z)) accD += w * L[dcode];
+                        unsigned long long hi = 0ull, lo = 0ull;
+                        if (c > 1u) clog2c_parts(c, a.tabfix, hi, lo);
+                        if (hi | lo) {
+                            atomicAdd(&wacc[wid][kk][0], hi);
+                            atomicAdd(&wacc[wid][kk][1], lo);
+                        }
+                    }
+                }
+            };
             if (MODE == WALK_STATS) {
-                // lanes 0-1 hold the strings of length 1, 2-5 length 2, 6-13 length 3, 14-29 length 4
-                const uint32_t bal = __ballot_sync(FULL, valid);
+                // lanes 0-1 hold the strings of length 1, 2-5 length 2, 6-13
+                // length 3, 14-29 length 4; every lane one of length 5
+                const uint32_t bal = __ballot_sync(FULL, valid), bal5 = __ballot_sync(FULL, valid5);
                 if (lane == kc + 1) accN += (uint32_t)__popc(bal & 0x3u);
                 if (lane == kc + 2) accN += (uint32_t)__popc(bal & 0x3Cu);
                 if (lane == kc + 3) accN += (uint32_t)__popc(bal & 0x3FC0u);
                 if (lane == kc + 4) accN += (uint32_t)__popc(bal & 0x3FFFC000u);
-                if (valid && cnt > 1u) {  // (a count of 1 adds 1 log2 1 = 0)
-                    unsigned long long hi, lo;
-                    clog2c_parts(cnt, a.tabfix, hi, lo);
-                    if (hi | lo) {
-                        atomicAdd(&wacc[wid][kk][0], hi);
-                        atomicAdd(&wacc[wid][kk][1], lo);
-                    }
-                }
-            } else if (MODE == WALK_EMIT) {
-                if (valid && BDC_IN_RANGE(dcode, (size_t)2 << n, st_z)) a.emb[dcode] = cnt;
-            } else {
-                if (valid) {
-                    const double w = (double)cnt * kw[kk];
-                    if (w > 0.0 && BDC_IN_RANGE(dcode, (size_t)2 << n, st_z)) accD += w * L[dcode];
-                    unsigned long long hi = 0ull, lo = 0ull;
-                    if (cnt > 1u) clog2c_parts(cnt, a.tabfix, hi, lo);
-                    if (hi | lo) {
-                        atomicAdd(&wacc[wid][kk][0], hi);
-                        atomicAdd(&wacc[wid][kk][1], lo);
-                    }
-                }
+                if (lane == kc + 5) accN += (uint32_t)__popc(bal5);
             }
+            leaf(valid, (ccode << zm) | (zc - (1u << zm)), kc + zm, cnt);
+            leaf(valid5, (ccode << 5) | (uint32_t)lane, kc + 5, cnt5);
         };
         while (sp > 0) {
             sp--;
