@@ -162,6 +162,18 @@ __global__ void k_check_p(int n, const double *p, uint32_t *flags, double *part,
 }
 
 // p <- p / sum p per instance, the sum taken from the nb block partials of
+// flags[z] |= 1 where some p(x) differs from p(cpl x) (bitwise)
+__global__ void k_check_cpl(int n, const double *p, uint32_t *flags) {
+    const int z = blockIdx.y;
+    const size_t N = (size_t)1 << n, full = N - 1;
+    const double *pz = p + z * N;
+    uint32_t f = 0;
+    for (size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x; x < N / 2; x += (size_t)gridDim.x * blockDim.x)
+        if (pz[x] != pz[x ^ full]) f = 1u;
+    f = __reduce_or_sync(0xffffffffu, f);
+    if ((threadIdx.x & 31) == 0 && f) atomicOr(flags + z, f);
+}
+
 // k_check_p (in block order: every CTA forms the same value)
 __global__ void k_normalize_p(int n, double *p, const double *part, int maxblk, int nb) {
     __shared__ double red[FIN_THREADS / 32];
@@ -1011,6 +1023,12 @@ extern "C" bdc_status bdc_certify_upper(bdc_engine *e, const double *q_dev, doub
     BDC_TRY(materialize(e));
     BDC_TRY(activate(e, -1.0));
     const double *Lsrc;
+    // complement half mode when the certified input is exactly complement-
+    // invariant (checked bitwise): q~ is then exactly invariant too (its H1
+    // codes are computed and mirrored), so D(cpl x) = D(x) for the q~ used and
+    // the max over the stored half of the inputs is the max over all of them;
+    // the lower bound's two sums cover the same half (a ratio)
+    bool half = false;
     int g0 = std::min(maxblk, grid_for(M, 256, 1024));
     double per_thread = std::ceil((double)M / ((double)g0 * 256.0));
     double Kterms = per_thread + 8.0 + g0;
@@ -1032,7 +1050,19 @@ extern "C" bdc_status bdc_certify_upper(bdc_engine *e, const double *q_dev, doub
                                                                            e->pcert); e->launches++;
         }
         BDC_CUDA_TRY(cudaGetLastError());
-        BDC_TRY(sweep_forward<double>(e, b, e->pcert, 0, MODE_CERT));  // q_k and L = log2 min(q_k, 1)
+        if (e->opt.use_half && half_possible(b.s)) {
+            std::vector<uint32_t> flags(nd);
+            BDC_CUDA_TRY(cudaMemsetAsync(e->pflags, 0, nd * sizeof(uint32_t), e->stream));
+            k_check_cpl<<<dim3(grid_for(N / 2, 256, 1024), nd), 256, 0, e->stream>>>(n, e->pcert, e->pflags);
+            e->launches++;
+            BDC_CUDA_TRY(cudaGetLastError());
+            BDC_CUDA_TRY(cudaMemcpyAsync(flags.data(), e->pflags, nd * sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                                         e->stream));
+            BDC_TRY(sync_check(e, "bdc_certify_upper"));
+            half = true;
+            for (int z = 0; z < nd; z++) half = half && flags[z] == 0u;
+        }
+        BDC_TRY(sweep_forward<double>(e, b, e->pcert, 0, MODE_CERT, half));  // q_k and L = log2 min(q_k, 1)
         k_sum_rows<double><<<dim3(g0, nd), 256, 0, e->stream>>>(b.q, M, b.part, maxblk, 2, e->bk, n); e->launches++;
         Lsrc = b.L;
     } else {
@@ -1042,9 +1072,9 @@ extern "C" bdc_status bdc_certify_upper(bdc_engine *e, const double *q_dev, doub
         Lsrc = b.aux;
     }
     BDC_CUDA_TRY(cudaGetLastError());
-    BDC_TRY(sweep_adjoint<double>(e, b, Lsrc, b.omega, e->marg, MODE_CERT));
-    k_finalize_cert<<<nd, FIN_THREADS, 0, e->stream>>>(nd, b.part, maxblk, g0, b.s.nblk_cols, Kterms, q_dev ? 0 : 1,
-                                                       e->inst); e->launches++;
+    BDC_TRY(sweep_adjoint<double>(e, b, Lsrc, b.omega, e->marg, MODE_CERT, half));
+    k_finalize_cert<<<nd, FIN_THREADS, 0, e->stream>>>(nd, b.part, maxblk, g0, half ? b.s.nblk_cols / 2 : b.s.nblk_cols,
+                                                       Kterms, q_dev ? 0 : 1, e->inst); e->launches++;
     BDC_CUDA_TRY(cudaGetLastError());
     std::vector<double> h;
     BDC_TRY(read_inst(e, h));

@@ -196,3 +196,49 @@ def test_dual_bound_split_schedule(n, d, tau, n2):
     assert abs(gd - gd_ref) <= 1e-9 * max(1.0, abs(gd_ref))
     assert mD <= F <= mD + tau * n + 1e-12
     eng.close()
+
+
+# ---------------------------------------------------------------------------
+# (e) the certificate's two forms on split schedules: a complement-invariant
+# input is certified in the complement half mode (checked bitwise on the
+# device), any other input over all inputs
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n,d,n2", [(12, 0.6, 7), (14, 0.45, 0), (16, 0.8, 0)])
+def test_certificate_half_mode_matches_full_mode(n, d, n2):
+    kw = dict(enable_literal=0)
+    if n2:
+        kw.update(sched_n2_fp64=n2, sched_w_fp64=2)
+    a = _engine(n, [d], **kw)
+    assert a.schedule("fp64")["n2"] > 0
+    a.iterate(15, -1.0, "fp64", "sweep")
+    ca = a.certify()
+    p = a.get_p()
+    assert np.array_equal(p[0], p[0][::-1])  # complement-invariant: p(x) = p(2^n - 1 - x)
+    a.close()
+    b = _engine(n, [d], use_half=0, **kw)  # the same input, certified over all inputs
+    b.set_p(p)
+    cb = b.certify()
+    b.close()
+    assert abs(ca["upper"][0] - cb["upper"][0]) <= 1e-11, (ca, cb)
+    assert abs(ca["lower"][0] - cb["lower"][0]) <= 1e-11
+    pt = (1 - EPS_CERT) * p[0] / p[0].sum() + EPS_CERT / (1 << n)
+    U_ref, _ = oracle.certify(n, d, oracle.q_full(n, d, pt))
+    assert U_ref - 1e-12 <= ca["upper"][0] <= U_ref + 1e-6
+
+
+@pytest.mark.parametrize("n,d,n2", [(12, 0.7, 7), (14, 0.3, 0)])
+def test_certificate_asymmetric_input_split_schedule(n, d, n2):
+    rng = np.random.default_rng(7 + n)
+    p = rng.uniform(0.2, 1.0, size=(1, 1 << n))
+    kw = dict(enable_literal=0)
+    if n2:
+        kw.update(sched_n2_fp64=n2, sched_w_fp64=2)
+    eng = _engine(n, [d], **kw)
+    assert eng.schedule("fp64")["n2"] > 0
+    eng.set_p(p)
+    c = eng.certify()
+    eng.close()
+    pt = (1 - EPS_CERT) * p[0] / p[0].sum() + EPS_CERT / (1 << n)
+    U_ref, _ = oracle.certify(n, d, oracle.q_full(n, d, pt))
+    assert U_ref - 1e-12 <= c["upper"][0] <= U_ref + 1e-6, (c, U_ref)
+    assert 0 < c["margin"][0] < 1e-6
