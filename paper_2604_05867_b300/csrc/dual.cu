@@ -61,12 +61,13 @@ __global__ void k_theta_sumexp(size_t M, const T *theta, const int32_t *cls, con
 // op 0: max of part[b*4+slot] -> inst[dst]
 // op 1: inst[dst] = inst[dst] + log(sum part[b*4+slot])       (log-sum-exp of theta)
 // op 2: inst[dst] = sum part[b*4+slot]
+// op 3: inst[dst] = 2 sum part[b*4+slot]    (a complement half of the inputs)
 __global__ void k_fin(const double *part, int stride4, int nb, int slot, double *inst_z, int dst, int op) {
     __shared__ double red[FIN_THREADS / 32];
     double acc = (op == 0) ? fin_max(part + slot, stride4, nb, red) : fin_sum(part + slot, stride4, nb, red);
     if (threadIdx.x != 0) return;
     if (op == 1) inst_z[dst] = inst_z[dst] + log(acc);
-    else inst_z[dst] = acc;
+    else inst_z[dst] = (op == 3) ? 2.0 * acc : acc;
 }
 
 template <typename T>
@@ -156,9 +157,15 @@ bdc_status dual_impl(bdc_engine *e, PrecBuf<T> &b, int z, const T *theta, double
     k_fin<<<1, FIN_THREADS, 0, e->stream>>>(part0, 4, gM, 1, iz, I_DUAL_ZT, 1); e->launches++;
     k_make_L<T><<<gM, RT, 0, e->stream>>>(M, theta, e->ocls, iz, Lz); e->launches++;
     BDC_CUDA_TRY(cudaGetLastError());
+    // q is constant on output classes, which are closed under complement, so
+    // L(cpl c) = L(c) exactly and D(cpl x) = D(x): the sweeps run in the
+    // complement half mode where the schedule allows, and D is mirrored
+    const bool half = e->opt.use_half && half_possible(b.s);
+    const int nbc = half ? b.s.nblk_cols / 2 : b.s.nblk_cols;
     // D_x for every input (double, into the spare array), block maxima
-    BDC_TRY(sweep_adjoint<T>(e, b, b.aux, b.omega, reinterpret_cast<T *>(e->marg), MODE_DUAL));
-    k_fin<<<1, FIN_THREADS, 0, e->stream>>>(part1, 4, b.s.nblk_cols, 1, iz, I_DUAL_MAXD, 0); e->launches++;
+    BDC_TRY(sweep_adjoint<T>(e, b, b.aux, b.omega, reinterpret_cast<T *>(e->marg), MODE_DUAL, half));
+    if (half) BDC_TRY(launch_mirror_half<double>(e, e->marg, b.s.n2));
+    k_fin<<<1, FIN_THREADS, 0, e->stream>>>(part1, 4, nbc, 1, iz, I_DUAL_MAXD, 0); e->launches++;
     const double *Dz = e->marg + z * N;
     k_pi_sum<<<gN, RT, 0, e->stream>>>(N, Dz, iz, tau, part0); e->launches++;
     k_fin<<<1, FIN_THREADS, 0, e->stream>>>(part0, 4, gN, 0, iz, I_DUAL_S, 2); e->launches++;
@@ -166,7 +173,7 @@ bdc_status dual_impl(bdc_engine *e, PrecBuf<T> &b, int z, const T *theta, double
     BDC_CUDA_TRY(cudaGetLastError());
     if (grad) {
         // q_k^pi = P_{n,k}^T pi by the forward sweep (no BA update)
-        BDC_TRY(sweep_forward<T>(e, b, b.pd, 0, MODE_DUAL));
+        BDC_TRY(sweep_forward<T>(e, b, b.pd, 0, MODE_DUAL, half));
         k_grad_theta<T><<<gridc((size_t)e->Rout), RT, 0, e->stream>>>(e->Rout, e->oreps, b.q + z * M, Lz,
                                                                        e->bk + (size_t)z * (n + 1), grad);
         e->launches++;
@@ -175,8 +182,8 @@ bdc_status dual_impl(bdc_engine *e, PrecBuf<T> &b, int z, const T *theta, double
     if (grad_d) {
         // sum_x pi_x (-Hb'(x) - G'(x)), Hb' = sum_k rho_k b_k H_k, G' with weights rho_k b_k / C(n,k)
         BDC_TRY(launch_build_Hb_w(e, e->dual_w, e->pcert));
-        BDC_TRY(sweep_adjoint<T>(e, b, b.aux, b.omega2, reinterpret_cast<T *>(e->marg), MODE_DUAL_D));
-        k_fin<<<1, FIN_THREADS, 0, e->stream>>>(part1, 4, b.s.nblk_cols, 0, iz, I_DUAL_GD, 2); e->launches++;
+        BDC_TRY(sweep_adjoint<T>(e, b, b.aux, b.omega2, reinterpret_cast<T *>(e->marg), MODE_DUAL_D, half));
+        k_fin<<<1, FIN_THREADS, 0, e->stream>>>(part1, 4, nbc, 0, iz, I_DUAL_GD, half ? 3 : 2); e->launches++;
         BDC_CUDA_TRY(cudaGetLastError());
     }
     std::vector<double> h(INST_STRIDE);
