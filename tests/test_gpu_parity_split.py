@@ -1,8 +1,9 @@
 """GPU parity against the oracle on the code paths the kernels take at full
 size: the split (columns, rows, combine) schedules, the stepped FP32
 iteration boundary in the headline configuration's column kernel, the
-literal enumeration path at sizes with many work items per class, and the
-smoothed dual bound on a split FP64 schedule.
+literal enumeration path at sizes with many work items per class, the
+smoothed dual bound on a split FP64 schedule, and the certificate's two forms
+(complement half mode for a complement-invariant input, all inputs otherwise).
 
 Bars (Sec. 2.3 quantities): certified bound U in [U_oracle - 1e-12,
 U_oracle + 1e-6] bits and U >= the oracle's BA lower bound; FP64 q 1e-12
