@@ -153,3 +153,25 @@ def test_full_size_bench_configuration():
         r = oracle.D_point(n, d, q, int(x))
         assert abs(D[x] - r) <= 1e-11 * max(1.0, abs(r))
     eng.close()
+
+
+def test_large_sweep_size_n26():
+    # n = 26, the large sweep's size, in its launch configuration (FP32 stepped
+    # iterations on the default schedule); then the FP64 q and D of the result
+    # at sampled outputs and inputs against the oracle, each computed one by
+    # one from its definition
+    n, d = 26, 0.8
+    eng = _engine(n, [d], enable_literal=0)
+    eng.iterate(2, -1.0, "fp32", "sweep")
+    lo, up = eng.history(0)
+    assert len(lo) == 2 and np.all(lo <= up)
+    p = eng.get_p()[0]
+    q = eng.get_q("fp64")[0]
+    for c in [int((1 << 7) | 0b1011001), int(inputs.random_codes(n, 1, seed=21)[0])]:
+        r = oracle.q_point(n, d, p, c)
+        assert abs(q[c] - r) <= 1e-12 * r
+    D = eng.divergence(precision="fp64").cpu().numpy()[0]
+    for x in inputs.random_inputs(n, 6, seed=22):
+        r = oracle.D_point(n, d, q, int(x))
+        assert abs(D[x] - r) <= 1e-11 * max(1.0, abs(r))
+    eng.close()
