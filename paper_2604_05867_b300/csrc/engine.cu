@@ -161,7 +161,6 @@ __global__ void k_check_p(int n, const double *p, uint32_t *flags, double *part,
     }
 }
 
-// p <- p / sum p per instance, the sum taken from the nb block partials of
 // flags[z] |= 1 where some p(x) differs from p(cpl x) (bitwise)
 __global__ void k_check_cpl(int n, const double *p, uint32_t *flags) {
     const int z = blockIdx.y;
@@ -174,6 +173,7 @@ __global__ void k_check_cpl(int n, const double *p, uint32_t *flags) {
     if ((threadIdx.x & 31) == 0 && f) atomicOr(flags + z, f);
 }
 
+// p <- p / sum p per instance, the sum taken from the nb block partials of
 // k_check_p (in block order: every CTA forms the same value)
 __global__ void k_normalize_p(int n, double *p, const double *part, int maxblk, int nb) {
     __shared__ double red[FIN_THREADS / 32];
