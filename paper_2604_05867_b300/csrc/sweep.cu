@@ -1016,16 +1016,18 @@ __global__ void k_combine(SweepArgs a, const T *__restrict__ p, const T *__restr
 // The same combine with the codes laid out by length: every CTA holds up to
 // CMB_CODES consecutive codes of one length k, so the split range, the source
 // array of each split and every shift are uniform across the CTA, and a term
-// costs a few integer operations and one load; each thread takes
-// CMB_CODES / 256 codes, 256 apart.  Codes of length k: 2^(k-1) in half mode
-// (those starting with 0), 2^k otherwise.  Each length below KB has a CTA of
-// its own (a CTA's splits run one after another, so these short lengths with
-// their many splits must not queue behind each other); longer lengths fill
-// CTAs of CMB_CODES codes.  1024 codes per CTA measured best at n = 24 (2048:
-// +22%, 512: +35%).
-constexpr int CMB_LOG = 10, CMB_CODES = 1 << CMB_LOG;
+// costs a few integer operations and one load; each of the CMB_THREADS
+// threads takes CMB_CODES / CMB_THREADS codes, CMB_THREADS apart.  Codes of
+// length k: 2^(k-1) in half mode (those starting with 0), 2^k otherwise.
+// Each length below KB has a CTA of its own (a CTA's splits run one after
+// another, so these short lengths with their many splits must not queue
+// behind each other); longer lengths fill CTAs of CMB_CODES codes.  Measured
+// at n = 24 (FP32): 512 codes on 128 threads 47.5 us; 1024 on 256 50 us, 2048
+// on 512 53 us, 256 on 64 49 us; two codes a thread (512 on 256, 256 on 128)
+// 74-76 us, eight (1024 on 128) 59 us.
+constexpr int CMB_LOG = 9, CMB_CODES = 1 << CMB_LOG, CMB_THREADS = 128;
 template <typename T, bool HALF>
-__global__ void __launch_bounds__(256) k_combine_k(SweepArgs a, const T *__restrict__ p, const T *__restrict__ F1,
+__global__ void __launch_bounds__(CMB_THREADS) k_combine_k(SweepArgs a, const T *__restrict__ p, const T *__restrict__ F1,
                                                    const T *__restrict__ Tm, const T *__restrict__ Ts,
                                                    T *__restrict__ q, T *__restrict__ L, int mode) {
     constexpr int KB = CMB_LOG + (HALF ? 1 : 0);
@@ -1050,9 +1052,9 @@ __global__ void __launch_bounds__(256) k_combine_k(SweepArgs a, const T *__restr
         const uint32_t cnt = (k == 0) ? 1u : (HALF ? 1u << (k - 1) : 1u << k);
         const uint32_t y0 = small ? 0u : ((bb - KB + 1) - (1u << (k - KB))) << CMB_LOG;
         const int jlo = max(0, k - n2), jhi = min(k, n1);
-        // the thread's CMB_CODES / 256 codes advance through the splits
+        // the thread's CMB_CODES / CMB_THREADS codes advance through the splits
         // together: their loads of one split are independent and in flight at once
-        constexpr int RC = CMB_CODES / 256;
+        constexpr int RC = CMB_CODES / CMB_THREADS;
         T acc[RC];
 #pragma unroll
         for (int r = 0; r < RC; r++) acc[r] = (T)0;
@@ -1088,14 +1090,14 @@ __global__ void __launch_bounds__(256) k_combine_k(SweepArgs a, const T *__restr
                 (void)ext;
 #pragma unroll
                 for (int r = 0; r < RC; r++) {
-                    const int off = sgn * (int)(r * 256 + threadIdx.x);
+                    const int off = sgn * (int)(r * CMB_THREADS + threadIdx.x);
                     if (BDC_IN_RANGE((src - arr) + off, ext, a.inst + z * INST_STRIDE)) acc[r] += src[off];
                 }
                 continue;
             }
 #pragma unroll
             for (int r = 0; r < RC; r++) {
-                const uint32_t y = y0 + r * 256 + threadIdx.x;
+                const uint32_t y = y0 + r * CMB_THREADS + threadIdx.x;
                 if (y >= cnt) break;
                 uint32_t c1 = (1u << j) | (y >> l);
                 uint32_t u2 = y & ((1u << l) - 1u);
@@ -1122,7 +1124,7 @@ __global__ void __launch_bounds__(256) k_combine_k(SweepArgs a, const T *__restr
         if (!active) return;
 #pragma unroll
         for (int r = 0; r < RC; r++) {
-            const uint32_t y = y0 + r * 256 + threadIdx.x;
+            const uint32_t y = y0 + r * CMB_THREADS + threadIdx.x;
             if (y >= cnt) break;
             const T accr = acc[r];
             const uint32_t c = (1u << k) | y;
@@ -2063,8 +2065,8 @@ bdc_status sweep_forward(bdc_engine *e, PrecBuf<T> &b, const T *p_src, int apply
         // blocks of CMB_CODES codes of one length (k_combine_k)
         const int kb = CMB_LOG + (half ? 1 : 0);
         dim3 g3(e->n >= kb ? (1u << (e->n - kb + 1)) - 1u + kb : (unsigned)e->n + 1u, e->nd);
-        if (half) k_combine_k<T, true><<<g3, 256, 0, e->stream>>>(a, p, b.F1, b.Tm, b.Ts, b.q, b.L, mode);
-        else k_combine_k<T, false><<<g3, 256, 0, e->stream>>>(a, p, b.F1, b.Tm, b.Ts, b.q, b.L, mode);
+        if (half) k_combine_k<T, true><<<g3, CMB_THREADS, 0, e->stream>>>(a, p, b.F1, b.Tm, b.Ts, b.q, b.L, mode);
+        else k_combine_k<T, false><<<g3, CMB_THREADS, 0, e->stream>>>(a, p, b.F1, b.Tm, b.Ts, b.q, b.L, mode);
         e->launches++; stage_mark(e, "combine");
         BDC_CUDA_TRY(cudaGetLastError());
     }
