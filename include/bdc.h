@@ -206,9 +206,13 @@ bdc_status bdc_divergence(bdc_engine *eng, const void *q_dev, int precision, dou
  * array [nd][2^(n+1)] of doubles (positive at every code).  Host arrays of
  * nd: upper (the certified bound, rounded up), margin (the added rounding
  * margin, bits), lower (FP64 Blahut lower bound of the current p; NaN when
- * q_dev is given).  Any may be NULL.  Errors: BDC_ENONFINITE (a NaN or Inf
- * in the given q, or a non-finite bound), BDC_EINVAL (a given q that is not
- * positive at every code); the values of the other instances are valid. */
+ * q_dev is given).  Any may be NULL.  When every instance's mixed input is
+ * exactly complement-invariant (checked on the device; true for BA iterates
+ * from a complement-invariant start) and the FP64 schedule splits, the two
+ * FP64 sweeps compute half of the values and mirror the rest (use_half = 0
+ * turns this off); the bound is the same.  Errors: BDC_ENONFINITE (a NaN or
+ * Inf in the given q, or a non-finite bound), BDC_EINVAL (a given q that is
+ * not positive at every code); the values of the other instances are valid. */
 bdc_status bdc_certify_upper(bdc_engine *eng, const double *q_dev, double *upper, double *margin, double *lower);
 
 /* --- state access (caller-owned host buffers, copied) -------------------- */
