@@ -298,10 +298,12 @@ def run_ours(args, rank: int, world: int):
         clocks.start()
         # keep the GPU under load (untimed iterations) while the sampler starts:
         # after half a second idle the first kernels run measurably slower (the
-        # forward rows pass by up to 20% for a while), so the timed steps follow
-        # load, not an idle gap; then the W warm-up steps again
+        # forward rows pass by up to 20% for a while), and on a GPU fresh to this
+        # process half a second of load still left the timed steps 2% slower
+        # than two seconds do, so the timed steps follow two seconds of load;
+        # then the W warm-up steps again
         t_load = time.perf_counter()
-        while time.perf_counter() - t_load < 0.5:
+        while time.perf_counter() - t_load < 2.0:
             eng.iterate(chunk, -1.0, "fp32", "sweep")
             torch.cuda.synchronize()
         eng.iterate(args.warmup, -1.0, "fp32", "sweep")
